@@ -1,0 +1,167 @@
+/*
+ * gridder.h: C ABI of the GB300 convolutional gridder (Merry 2016, "Faster
+ * GPU-based convolutional gridding via thread coarsening").
+ *
+ * Gridding (Sec. 2.2) treats every visibility as a Dirac delta. It convolves
+ * the delta with an oversampled, separable gridding convolution function
+ * (GCF, Sec. 2.2 and Sec. 4) and accumulates the result on a regular G x G
+ * complex grid, one plane per polarization. The GPU kernels use Romein's
+ * sliding-window work distribution (Sec. 2.2, Fig. 1) with thread coarsening
+ * (Sec. 3, Fig. 2): each thread owns a Bu x Bv block of grid points and keeps
+ * register accumulators, which it flushes with atomic adds only when the
+ * visibility's bounding box moves off its block. Degridding is built as the
+ * exact adjoint.
+ *
+ * Conventions (for every entry point):
+ *  - uv: [n][2] float64 (u, v) in grid-pixel units relative to the grid
+ *    centre. Cell G/2 holds u = 0.
+ *  - Fine position: f = floor(u*O + 1/2), evaluated exactly on the float64
+ *    input. Centre cell: C = floor((f + O/2)/O) + G/2. Table row:
+ *    r = f - (C - G/2)*O + O/2, in [0, O).
+ *  - Footprint: cells C-h .. C-h+S-1 per axis, with h = (S-1)/2. A
+ *    visibility whose footprint is not wholly inside the grid, or whose
+ *    coordinates are not finite, is skipped and counted.
+ *  - Tap (i, j) of a visibility is table[r_u][i] * table[r_v][j].
+ *  - Layouts:
+ *    - vis: [n][npol] complex, interleaved (re, im). Stored as float32
+ *      (GRID_PREC_F32), or as bf16 / fp16 pairs.
+ *    - weights: [n] float32.
+ *    - kernel_table: [O][S] real, float32, or bf16 / fp16 to match the
+ *      plan's precision.
+ *    - grid: [npol][G][G] complex64, row index v, column index u.
+ *  - Every data pointer is a caller-owned DEVICE pointer. It is borrowed until
+ *    the work queued on `stream` completes. Calls are asynchronous on
+ *    `stream`; a device fault surfaces at the caller's next synchronisation.
+ *  - Return value: GRID_OK (0) or a negative GRID_ERR_* code. The message of
+ *    the last error on the calling thread is in grid_last_error(). Nothing
+ *    aborts the process.
+ */
+#ifndef GB300_GRIDDER_H
+#define GB300_GRIDDER_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grid_plan_s* grid_plan_t;
+
+enum {
+  GRID_OK = 0,
+  GRID_ERR_INVALID = -1,     /* bad argument: size, null or misaligned pointer, range */
+  GRID_ERR_UNSUPPORTED = -2, /* valid, but no kernel is built for it (for example a too large Bu*Bv*npol) */
+  GRID_ERR_NOMEM = -3,       /* device allocation of plan scratch failed */
+  GRID_ERR_CUDA = -4         /* a CUDA runtime call or kernel launch failed */
+};
+
+/* Storage precision of vis and kernel_table (NEXT-1). Accumulation is always FP32. */
+enum { GRID_PREC_F32 = 0, GRID_PREC_BF16 = 1, GRID_PREC_F16 = 2 };
+
+/* Work distribution. */
+enum {
+  /* Sec. 4: fixed-size chunks of baseline-ordered visibilities, one team of
+   * threads per chunk. Flushes go straight to the grid in global memory with
+   * atomic adds. */
+  GRID_SCHED_CHUNKED = 0,
+  /* The same chunks, first binned by the grid "patch" (a square region of
+   * the grid) their footprints start in. A CTA accumulates one patch plus a
+   * halo in shared memory. Register flushes that land there use shared
+   * atomics, and flushes that land outside it go to global memory. The patch
+   * reaches the grid once per work item, with coalesced vector atomics. */
+  GRID_SCHED_PATCH = 1
+};
+
+typedef struct {
+  int G;            /* grid side, even, 2 .. 65536 */
+  int S;            /* GCF support (taps per axis), 1 .. 64, S <= G */
+  int oversample;   /* O, a power of two, 1 .. 256 */
+  int npol;         /* polarizations P: 1, 2 or 4 */
+  int Bu, Bv;       /* coarsening (block) factors per axis, 1 .. 8; (1, 1) is Romein's plain algorithm */
+  int vis_per_chunk;/* visibilities per team chunk (Sec. 4 uses 1024); 0 = default */
+  int threads;      /* threads per CTA target; 0 = default (256) */
+  int precision;    /* GRID_PREC_* */
+  int schedule;     /* GRID_SCHED_* */
+  int patch;        /* GRID_SCHED_PATCH: patch side in cells; 0 = default */
+} grid_plan_desc;
+
+/* Fill `desc` with the defaults for the given problem and coarsening B (Bu = Bv = B). */
+void grid_plan_desc_init(grid_plan_desc* desc, int G, int S, int oversample, int npol, int B);
+
+/*
+ * Create a plan (host call). It validates the problem, derives the bin
+ * geometry (bin width per axis N_b = roundup(S + B - 1, B), Sec. 3), picks the
+ * team shape and allocates the plan's device scratch on the current device.
+ * The plan is bound to that device.
+ * On success *out holds a plan the caller owns and destroys with
+ * grid_plan_destroy().
+ */
+int grid_plan_create(grid_plan_t* out, int G, int S, int oversample, int npol, int B);
+int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* desc);
+
+/* Destroy a plan and free its device scratch. NULL is allowed. The caller
+ * must make sure no queued work still uses it. */
+void grid_plan_destroy(grid_plan_t plan);
+
+/* Copy the plan's resolved parameters (bin widths, team size, ...) into desc. */
+int grid_plan_describe(grid_plan_t plan, grid_plan_desc* desc, int* bin_u, int* bin_v, int* team_size);
+
+/*
+ * Gridding (Sec. 2.2; kernels: Sec. 3 and Sec. 4):
+ *   grid[p][C_v-h+j][C_u-h+i] += w_n * vis[n][p] * table[r_u][i] * table[r_v][j]
+ * for every valid visibility n, polarization p and tap (i, j). ACCUMULATES
+ * into grid, which the caller zeroes when a fresh grid is wanted.
+ * weights may be NULL (unit weights). n_vis may be 0. Visibilities should be
+ * ordered by baseline and time (Sec. 4); any order gives the same sums, only
+ * more slowly.
+ */
+int grid(grid_plan_t plan, int64_t n_vis, const double* uv, const void* vis, const float* weights,
+         const void* kernel_table, void* grid, cudaStream_t stream);
+
+/*
+ * Degridding, the adjoint of gridding with unit weights:
+ *   vis[n][p] = sum_{i,j} table[r_u][i] * table[r_v][j] * grid[p][C_v-h+j][C_u-h+i]
+ * The paper proposes it as future work (Sec. 6). OVERWRITES vis (always
+ * complex64, [n][npol]). A skipped visibility gets 0.
+ */
+int degrid(grid_plan_t plan, int64_t n_vis, const double* uv, const void* grid, const void* kernel_table,
+           void* vis, cudaStream_t stream);
+
+/*
+ * Oversampled Kaiser-Bessel table (Sec. 2.2: precomputed and oversampled).
+ * Writes [O][S] values to the DEVICE buffer table_out, in the plan precision
+ * `precision`:
+ *   table[r][i] = I0(beta*sqrt(1 - (2d/S)^2)) / I0(beta),  d = i - h - (r - O/2)/O,
+ * and 0 where |2d/S| > 1. The values are computed in FP64 on the device and
+ * rounded once.
+ */
+int grid_make_kernel_table(int S, int oversample, double beta, int precision, void* table_out, cudaStream_t stream);
+
+/*
+ * The per-visibility indices the kernels use, for bit-exact checking:
+ *   cell[n][2] = (C_u, C_v) and sub[n][2] = (r_u, r_v), or (-1, -1) for both
+ *   when the visibility is skipped.
+ * Device pointers, int32.
+ */
+int grid_compute_indices(grid_plan_t plan, int64_t n_vis, const double* uv, int32_t* cell, int32_t* sub,
+                         cudaStream_t stream);
+
+/*
+ * Number of visibilities skipped (invalid or off the grid) by the plan's calls
+ * since it was created or last reset. This synchronises with the plan's
+ * device counter. reset != 0 zeroes the counter afterwards.
+ */
+int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* grid_last_error(void);
+
+/* Peak FP32 FMA lanes per SM per clock (128 on sm_103) and the SM count of the current device. */
+int grid_device_info(int* sm_count, int* fma_lanes_per_sm, int* max_clock_khz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_GRIDDER_H */

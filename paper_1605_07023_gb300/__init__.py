@@ -1,0 +1,186 @@
+"""GB300-native convolutional gridding with Romein's sliding window and thread coarsening.
+
+A thin binding over the C ABI in ``include/gridder.h``. The functions keep the
+ABI's names and only marshal arguments: tensors must already live on the CUDA
+device, and all the work runs in the library's CUDA kernels on the caller's
+current stream. There is no CPU path; if the library is not built, every call
+raises RuntimeError.
+
+Layouts (see the header for the full contract):
+  - uv: [n, 2] float64, in grid pixels relative to the centre.
+  - vis: [n, P] complex64. For 16-bit storage, [n, P, 2] bfloat16 / float16.
+  - weights: [n] float32 or None.
+  - kernel_table: [O, S] float32 / bfloat16 / float16.
+  - grid: [P, G, G] complex64.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import GridderError, PREC, SCHED
+
+__all__ = ["Plan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "grid_make_kernel_table",
+           "grid_compute_indices", "device_info", "GridderError"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dptr(t, name: str, dtype=None, ndim=None) -> int:
+    torch = _torch()
+    if t is None:
+        return 0
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions, has {t.dim()}")
+    return t.data_ptr()
+
+
+class Plan:
+    """Owns one grid_plan_t (destroyed on close() or garbage collection)."""
+
+    def __init__(self, G: int, S: int, oversample: int, npol: int, B: int = 1, Bu: int | None = None,
+                 Bv: int | None = None, vis_per_chunk: int = 0, threads: int = 0, precision: str = "f32",
+                 schedule: str = "chunked", patch: int = 0):
+        lib = _lib.load()
+        d = _lib.GridPlanDesc()
+        lib.grid_plan_desc_init(ctypes.byref(d), G, S, oversample, npol, B)
+        d.Bu = B if Bu is None else Bu
+        d.Bv = B if Bv is None else Bv
+        d.vis_per_chunk = vis_per_chunk
+        d.threads = threads
+        d.precision = PREC[precision]
+        d.schedule = SCHED[schedule]
+        d.patch = patch
+        h = ctypes.c_void_p()
+        _lib.check(lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)))
+        self._h = h
+        self.G, self.S, self.oversample, self.npol = G, S, oversample, npol
+        self.precision = precision
+        self.schedule = schedule
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    def describe(self) -> dict:
+        d = _lib.GridPlanDesc()
+        bu, bv, ts = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(_lib.load().grid_plan_describe(self.handle, ctypes.byref(d), ctypes.byref(bu), ctypes.byref(bv),
+                                                  ctypes.byref(ts)))
+        out = {n: getattr(d, n) for n, _ in _lib.GridPlanDesc._fields_}
+        out.update(bin_u=bu.value, bin_v=bv.value, team_size=ts.value)
+        return out
+
+    def skipped(self, reset: bool = False) -> int:
+        v = ctypes.c_int64()
+        _lib.check(_lib.load().grid_plan_skipped(self.handle, ctypes.byref(v), int(reset)))
+        return v.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib.load().grid_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # convenience wrappers
+    def grid(self, uv, vis, weights, kernel_table, grid_out, stream=None):
+        return grid(self, uv, vis, weights, kernel_table, grid_out, stream)
+
+    def degrid(self, uv, grid_in, kernel_table, vis_out=None, stream=None):
+        return degrid(self, uv, grid_in, kernel_table, vis_out, stream)
+
+
+def grid_plan_create(G: int, S: int, oversample: int, npol: int, B: int = 1) -> Plan:
+    return Plan(G, S, oversample, npol, B)
+
+
+def grid_plan_create_ex(**kw) -> Plan:
+    return Plan(**kw)
+
+
+def _vis_dtype(plan: Plan):
+    torch = _torch()
+    return {"f32": torch.complex64, "bf16": torch.bfloat16, "f16": torch.float16}[plan.precision]
+
+
+def grid(plan: Plan, uv, vis, weights, kernel_table, grid_out, stream=None):
+    """grid(): accumulate the visibilities into grid_out ([P, G, G] complex64). Returns grid_out."""
+    torch = _torch()
+    n = uv.shape[0]
+    pu = _dptr(uv, "uv", torch.float64, 2)
+    pv = _dptr(vis, "vis", _vis_dtype(plan))
+    pw = _dptr(weights, "weights", torch.float32, 1)
+    pt = _dptr(kernel_table, "kernel_table", (torch.float32, torch.bfloat16, torch.float16), 2)
+    pg = _dptr(grid_out, "grid", torch.complex64, 3)
+    if vis.shape[0] != n or (weights is not None and weights.shape[0] != n):
+        raise ValueError("uv, vis and weights must have the same length")
+    if tuple(grid_out.shape) != (plan.npol, plan.G, plan.G):
+        raise ValueError(f"grid must be [{plan.npol}, {plan.G}, {plan.G}]")
+    _lib.check(_lib.load().grid(plan.handle, n, pu, pv, pw or None, pt, pg, _stream_ptr(stream)))
+    return grid_out
+
+
+def degrid(plan: Plan, uv, grid_in, kernel_table, vis_out=None, stream=None):
+    """degrid(): visibilities [n, P] complex64 from grid_in (overwrites vis_out). Returns vis_out."""
+    torch = _torch()
+    n = uv.shape[0]
+    if vis_out is None:
+        vis_out = torch.empty((n, plan.npol), dtype=torch.complex64, device=uv.device)
+    pu = _dptr(uv, "uv", torch.float64, 2)
+    pg = _dptr(grid_in, "grid", torch.complex64, 3)
+    pt = _dptr(kernel_table, "kernel_table", (torch.float32, torch.bfloat16, torch.float16), 2)
+    po = _dptr(vis_out, "vis", torch.complex64, 2)
+    if tuple(grid_in.shape) != (plan.npol, plan.G, plan.G):
+        raise ValueError(f"grid must be [{plan.npol}, {plan.G}, {plan.G}]")
+    _lib.check(_lib.load().degrid(plan.handle, n, pu, pg, pt, po, _stream_ptr(stream)))
+    return vis_out
+
+
+def grid_make_kernel_table(S: int, oversample: int, beta: float, precision: str = "f32", device=None, stream=None):
+    """Oversampled Kaiser-Bessel table [O, S], computed on the device in FP64 and rounded once."""
+    torch = _torch()
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[precision]
+    out = torch.empty((oversample, S), dtype=dt, device=device or "cuda")
+    _lib.check(_lib.load().grid_make_kernel_table(S, oversample, float(beta), PREC[precision], out.data_ptr(),
+                                                  _stream_ptr(stream)))
+    return out
+
+
+def grid_compute_indices(plan: Plan, uv, stream=None):
+    """(cell [n, 2] int32, sub [n, 2] int32) as the kernels compute them; -1 marks a skipped visibility."""
+    torch = _torch()
+    n = uv.shape[0]
+    cell = torch.empty((n, 2), dtype=torch.int32, device=uv.device)
+    sub = torch.empty((n, 2), dtype=torch.int32, device=uv.device)
+    _lib.check(_lib.load().grid_compute_indices(plan.handle, n, _dptr(uv, "uv", torch.float64, 2), cell.data_ptr(),
+                                                sub.data_ptr(), _stream_ptr(stream)))
+    return cell, sub
+
+
+def device_info() -> dict:
+    sms, lanes, clk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _lib.check(_lib.load().grid_device_info(ctypes.byref(sms), ctypes.byref(lanes), ctypes.byref(clk)))
+    return dict(sm_count=sms.value, fma_lanes_per_sm=lanes.value, max_clock_khz=clk.value)

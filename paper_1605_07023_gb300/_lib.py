@@ -1,0 +1,85 @@
+"""ctypes loader for libgb300gridder.so (the C ABI in include/gridder.h).
+
+There is no fallback. If the library is missing or cannot load, every entry
+point raises RuntimeError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgb300gridder.so")
+
+GRID_OK = 0
+GRID_ERR_INVALID = -1
+GRID_ERR_UNSUPPORTED = -2
+GRID_ERR_NOMEM = -3
+GRID_ERR_CUDA = -4
+
+PREC = {"f32": 0, "bf16": 1, "f16": 2}
+SCHED = {"chunked": 0, "patch": 1}
+
+EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
+           "grid", "degrid", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
+           "grid_last_error", "grid_device_info")
+
+
+class GridPlanDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("G", "S", "oversample", "npol", "Bu", "Bv", "vis_per_chunk", "threads",
+                                             "precision", "schedule", "patch")]
+
+
+class GridderError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gridder error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load the library (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} is missing. Run __graft_entry__.build() "
+                           "(or python paper_1605_07023_gb300/build.py) first.")
+    lib = ctypes.CDLL(p)
+    i32, i64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    pdesc = ctypes.POINTER(GridPlanDesc)
+    lib.grid_plan_desc_init.argtypes = [pdesc, i32, i32, i32, i32, i32]
+    lib.grid_plan_desc_init.restype = None
+    lib.grid_plan_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32]
+    lib.grid_plan_create.restype = i32
+    lib.grid_plan_create_ex.argtypes = [ctypes.POINTER(vp), pdesc]
+    lib.grid_plan_create_ex.restype = i32
+    lib.grid_plan_destroy.argtypes = [vp]
+    lib.grid_plan_destroy.restype = None
+    lib.grid_plan_describe.argtypes = [vp, pdesc, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.grid_plan_describe.restype = i32
+    lib.grid.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    lib.grid.restype = i32
+    lib.degrid.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    lib.degrid.restype = i32
+    lib.grid_make_kernel_table.argtypes = [i32, i32, ctypes.c_double, i32, vp, vp]
+    lib.grid_make_kernel_table.restype = i32
+    lib.grid_compute_indices.argtypes = [vp, i64, vp, vp, vp, vp]
+    lib.grid_compute_indices.restype = i32
+    lib.grid_plan_skipped.argtypes = [vp, ctypes.POINTER(i64), i32]
+    lib.grid_plan_skipped.restype = i32
+    lib.grid_last_error.argtypes = []
+    lib.grid_last_error.restype = ctypes.c_char_p
+    lib.grid_device_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.grid_device_info.restype = i32
+    _lib = lib
+    return lib
+
+
+def check(rc: int) -> None:
+    if rc != GRID_OK:
+        msg = load().grid_last_error().decode(errors="replace")
+        raise GridderError(rc, msg)

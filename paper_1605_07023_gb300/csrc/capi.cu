@@ -1,0 +1,402 @@
+// C ABI of the GB300 gridder: plan management, validation and kernel launch.
+// The declarations and their contracts are in include/gridder.h.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/gridder.h"
+#include "internal.h"
+
+using namespace gbg;
+
+struct grid_plan_s {
+  grid_plan_desc desc;
+  Geometry g;
+  int device;
+  int sm_count;
+  int threads;          // threads per CTA (tpc * ts)
+  int chunk_len;
+  const KernelEntry* k;
+  size_t smem_grid;     // dynamic shared memory of the gridding kernel
+  size_t smem_degrid;
+  int occ_grid;         // resident gridding CTAs per SM (patch schedule)
+  unsigned long long* d_skipped;
+  PatchScratch ps;
+  long long ps_chunks_cap;  // chunk capacity of the patch scratch
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GRID_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
+size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+const KernelEntry* find_kernel(int bu, int bv, int p) {
+  int n = 0;
+  const KernelEntry* t = p == 1 ? kernels_p1(&n) : p == 2 ? kernels_p2(&n) : p == 4 ? kernels_p4(&n) : nullptr;
+  for (int i = 0; t && i < n; ++i)
+    if (t[i].bu == bu && t[i].bv == bv) return &t[i];
+  return nullptr;
+}
+
+size_t tables_bytes(const Geometry& g, int bu, int bv) {
+  return a16((size_t)g.O * bu * g.nbu * 4) + a16((size_t)g.O * bv * g.nbv * 4);
+}
+
+size_t grid_smem(const Geometry& g, int bu, int bv, int win) {
+  size_t s = tables_bytes(g, bu, bv) + 2 * (size_t)g.tpc * kRB * (16 + 8 * g.P);
+  s = a16(s);
+  if (win > 0) s += (size_t)g.P * win * win * 8;
+  return s;
+}
+
+size_t degrid_smem(const Geometry& g, int bu, int bv) {
+  const int tsp = g.ts | 1;
+  return tables_bytes(g, bu, bv) + (size_t)g.tpc * kRBD * 16 + a16((size_t)g.tpc * kRBD * 2 * g.P * tsp * 4);
+}
+
+void free_patch(grid_plan_s* pl) {
+  PatchScratch& s = pl->ps;
+  cudaFree(s.patch_count); cudaFree(s.patch_off); cudaFree(s.chunk_patch); cudaFree(s.chunk_slot);
+  cudaFree(s.chunk_order); cudaFree(s.work); cudaFree(s.n_work); cudaFree(s.work_next);
+  s.patch_count = s.patch_off = s.chunk_patch = s.chunk_slot = s.chunk_order = s.n_work = s.work_next = nullptr;
+  s.work = nullptr;
+  pl->ps_chunks_cap = 0;
+}
+
+int ensure_patch_scratch(grid_plan_s* pl, long long n_chunks) {
+  if (n_chunks <= pl->ps_chunks_cap) return GRID_OK;
+  free_patch(pl);
+  PatchScratch& s = pl->ps;
+  const long long cap = n_chunks + n_chunks / 4 + 64;
+  s.max_work = (int)(s.n_patches + cap / s.max_chunks + 2);
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMalloc(&s.patch_count, sizeof(int) * s.n_patches);
+  e = e ? e : cudaMalloc(&s.patch_off, sizeof(int) * (s.n_patches + 1));
+  e = e ? e : cudaMalloc(&s.chunk_patch, sizeof(int) * cap);
+  e = e ? e : cudaMalloc(&s.chunk_slot, sizeof(int) * cap);
+  e = e ? e : cudaMalloc(&s.chunk_order, sizeof(int) * cap);
+  e = e ? e : cudaMalloc(&s.work, sizeof(int4) * s.max_work);
+  e = e ? e : cudaMalloc(&s.n_work, sizeof(int));
+  e = e ? e : cudaMalloc(&s.work_next, sizeof(int));
+  if (e != cudaSuccess) {
+    free_patch(pl);
+    return fail(GRID_ERR_NOMEM, "patch scratch allocation failed: %s", cudaGetErrorString(e));
+  }
+  pl->ps_chunks_cap = cap;
+  return GRID_OK;
+}
+
+// Pointer checks: non-null and aligned as the kernels' vector accesses need.
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+Args make_args(const grid_plan_s* pl, int64_t n_vis, const double* uv) {
+  Args a;
+  memset(&a, 0, sizeof a);
+  a.g = pl->g;
+  a.n_vis = n_vis;
+  a.uv = (const double2*)uv;
+  a.chunk_len = pl->chunk_len;
+  a.n_chunks = (n_vis + pl->chunk_len - 1) / pl->chunk_len;
+  a.skipped = pl->d_skipped;
+  a.vis_fmt = pl->desc.precision;
+  a.tab_fmt = pl->desc.precision;
+  return a;
+}
+
+int check_device(const grid_plan_s* pl) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != pl->device) return fail(GRID_ERR_INVALID, "plan was created on device %d, current device is %d", pl->device, dev);
+  return GRID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grid_last_error(void) { return g_err.c_str(); }
+
+void grid_plan_desc_init(grid_plan_desc* d, int G, int S, int oversample, int npol, int B) {
+  if (!d) return;
+  memset(d, 0, sizeof *d);
+  d->G = G; d->S = S; d->oversample = oversample; d->npol = npol; d->Bu = B; d->Bv = B;
+  d->vis_per_chunk = 0; d->threads = 0; d->precision = GRID_PREC_F32; d->schedule = GRID_SCHED_CHUNKED; d->patch = 0;
+}
+
+int grid_plan_create(grid_plan_t* out, int G, int S, int oversample, int npol, int B) {
+  grid_plan_desc d;
+  grid_plan_desc_init(&d, G, S, oversample, npol, B);
+  return grid_plan_create_ex(out, &d);
+}
+
+int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
+  g_err.clear();
+  if (!out || !din) return fail(GRID_ERR_INVALID, "null argument");
+  *out = nullptr;
+  grid_plan_desc d = *din;
+  if (d.G < 2 || d.G > 32768 || (d.G & 1)) return fail(GRID_ERR_INVALID, "G=%d: must be even, 2..32768", d.G);
+  if (d.S < 1 || d.S > 64 || d.S > d.G) return fail(GRID_ERR_INVALID, "S=%d: must be 1..64 and <= G", d.S);
+  if (!is_pow2(d.oversample) || d.oversample > 256) return fail(GRID_ERR_INVALID, "oversample=%d: must be a power of two <= 256", d.oversample);
+  if (d.npol != 1 && d.npol != 2 && d.npol != 4) return fail(GRID_ERR_INVALID, "npol=%d: must be 1, 2 or 4", d.npol);
+  if (d.Bu < 1 || d.Bu > 8 || d.Bv < 1 || d.Bv > 8) return fail(GRID_ERR_INVALID, "B=(%d,%d): must be 1..8", d.Bu, d.Bv);
+  if (d.precision < GRID_PREC_F32 || d.precision > GRID_PREC_F16) return fail(GRID_ERR_INVALID, "precision=%d", d.precision);
+  if (d.schedule != GRID_SCHED_CHUNKED && d.schedule != GRID_SCHED_PATCH) return fail(GRID_ERR_INVALID, "schedule=%d", d.schedule);
+  if (d.vis_per_chunk < 0 || d.vis_per_chunk > (1 << 20)) return fail(GRID_ERR_INVALID, "vis_per_chunk=%d", d.vis_per_chunk);
+  if (d.threads < 0 || d.threads > 1024) return fail(GRID_ERR_INVALID, "threads=%d", d.threads);
+  const KernelEntry* k = find_kernel(d.Bu, d.Bv, d.npol);
+  if (!k) return fail(GRID_ERR_UNSUPPORTED, "no kernel built for Bu=%d Bv=%d npol=%d", d.Bu, d.Bv, d.npol);
+
+  grid_plan_s* pl = new grid_plan_s;
+  memset(pl, 0, sizeof *pl);
+  pl->k = k;
+  Geometry& g = pl->g;
+  g.G = d.G; g.S = d.S; g.O = d.oversample; g.log2O = ilog2(d.oversample); g.h = (d.S - 1) / 2; g.P = d.npol;
+  g.nbu = ((d.S + d.Bu - 1 + d.Bu - 1) / d.Bu) * d.Bu;
+  g.nbv = ((d.S + d.Bv - 1 + d.Bv - 1) / d.Bv) * d.Bv;
+  g.nu = g.nbu / d.Bu;
+  g.nv = g.nbv / d.Bv;
+  g.ts = g.nu * g.nv;
+
+  cudaError_t e = cudaGetDevice(&pl->device);
+  if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, pl->device);
+  if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDeviceProperties"); }
+  pl->sm_count = prop.multiProcessorCount;
+  cudaFuncAttributes fa_g, fa_d;
+  e = cudaFuncGetAttributes(&fa_g, k->grid_fn);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa_d, k->degrid_fn);
+  if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncGetAttributes (is this an sm_103 GPU?)"); }
+  const int max_thr = fa_g.maxThreadsPerBlock < fa_d.maxThreadsPerBlock ? fa_g.maxThreadsPerBlock : fa_d.maxThreadsPerBlock;
+  if (g.ts > max_thr) {
+    const int ts = g.ts;
+    delete pl;
+    return fail(GRID_ERR_UNSUPPORTED, "team of %d threads exceeds the %d threads per CTA this kernel can run", ts, max_thr);
+  }
+  const int target = d.threads > 0 ? d.threads : 256;
+  g.tpc = target / g.ts;
+  if (g.tpc < 1) g.tpc = 1;
+  while (g.tpc > 1 && g.tpc * g.ts > max_thr) --g.tpc;
+  pl->threads = g.tpc * g.ts;
+
+  if (d.vis_per_chunk == 0) d.vis_per_chunk = d.schedule == GRID_SCHED_PATCH ? 64 : 1024;
+  pl->chunk_len = d.vis_per_chunk;
+
+  const size_t tb = tables_bytes(g, d.Bu, d.Bv);
+  if (tb > 96 * 1024) {
+    delete pl;
+    return fail(GRID_ERR_UNSUPPORTED, "padded GCF tables need %zu bytes of shared memory (> 96 KiB)", tb);
+  }
+  const size_t smem_max = prop.sharedMemPerBlockOptin;
+
+  int win = 0;
+  if (d.schedule == GRID_SCHED_PATCH) {
+    PatchScratch& s = pl->ps;
+    int patch = d.patch;
+    const int halo = 12;
+    if (patch <= 0) patch = d.npol == 4 ? 32 : d.npol == 2 ? 64 : 96;
+    patch = (patch + 1) & ~1;  // even, so window rows start on 16-byte boundaries
+    // shrink the patch until the window fits next to the tables and records
+    for (;;) {
+      win = patch + 2 * halo + (g.nbu > g.nbv ? g.nbu : g.nbv);
+      win = (win + 1) & ~1;
+      if (grid_smem(g, d.Bu, d.Bv, win) + 1024 <= smem_max || patch <= 8) break;
+      patch -= 8;
+    }
+    if (patch < 1 || grid_smem(g, d.Bu, d.Bv, win) + 1024 > smem_max) {
+      delete pl;
+      return fail(GRID_ERR_UNSUPPORTED, "patch window does not fit in shared memory");
+    }
+    d.patch = patch;
+    s.patch = patch;
+    s.n_pu = (g.G + patch - 1) / patch;
+    s.n_patches = s.n_pu * s.n_pu;
+    s.halo_lo = halo;
+    s.win = win;
+    s.max_chunks = 128;
+  }
+  pl->smem_grid = grid_smem(g, d.Bu, d.Bv, win);
+  pl->smem_degrid = degrid_smem(g, d.Bu, d.Bv);
+  if (pl->smem_grid > smem_max || pl->smem_degrid > smem_max) {
+    delete pl;
+    return fail(GRID_ERR_UNSUPPORTED, "kernel needs more shared memory than the device offers");
+  }
+  e = cudaFuncSetAttribute(k->grid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_grid);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k->degrid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_degrid);
+  if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute"); }
+  if (d.schedule == GRID_SCHED_PATCH) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occ_grid, k->grid_fn, pl->threads, pl->smem_grid);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
+    if (pl->occ_grid < 1) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "gridding kernel cannot be resident with this shape"); }
+  }
+  e = cudaMalloc(&pl->d_skipped, sizeof(unsigned long long));
+  if (e != cudaSuccess) { delete pl; return fail(GRID_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+  e = cudaMemset(pl->d_skipped, 0, sizeof(unsigned long long));
+  if (e != cudaSuccess) { cudaFree(pl->d_skipped); delete pl; return cuda_fail(e, "cudaMemset"); }
+  pl->desc = d;
+  *out = pl;
+  return GRID_OK;
+}
+
+void grid_plan_destroy(grid_plan_t pl) {
+  if (!pl) return;
+  free_patch(pl);
+  cudaFree(pl->d_skipped);
+  delete pl;
+}
+
+int grid_plan_describe(grid_plan_t pl, grid_plan_desc* desc, int* bin_u, int* bin_v, int* team_size) {
+  if (!pl) return fail(GRID_ERR_INVALID, "null plan");
+  if (desc) { *desc = pl->desc; desc->threads = pl->threads; }
+  if (bin_u) *bin_u = pl->g.nbu;
+  if (bin_v) *bin_v = pl->g.nbv;
+  if (team_size) *team_size = pl->g.ts;
+  return GRID_OK;
+}
+
+int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const float* weights, const void* kernel_table,
+         void* grid_out, cudaStream_t stream) {
+  g_err.clear();
+  if (!pl) return fail(GRID_ERR_INVALID, "null plan");
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
+  if (!kernel_table || !grid_out) return fail(GRID_ERR_INVALID, "null kernel_table or grid");
+  if (!aligned(grid_out, 16)) return fail(GRID_ERR_INVALID, "grid must be 16-byte aligned");
+  if (n_vis == 0) return GRID_OK;
+  if (!uv || !vis) return fail(GRID_ERR_INVALID, "null uv or vis");
+  if (!aligned(uv, 16)) return fail(GRID_ERR_INVALID, "uv must be 16-byte aligned");
+  const size_t vbytes = (pl->desc.precision == GRID_PREC_F32 ? 8 : 4) * (size_t)pl->g.P;
+  if (!aligned(vis, vbytes >= 16 ? 16 : vbytes)) return fail(GRID_ERR_INVALID, "vis must be %zu-byte aligned", vbytes >= 16 ? (size_t)16 : vbytes);
+  if (weights && !aligned(weights, 4)) return fail(GRID_ERR_INVALID, "weights must be 4-byte aligned");
+  int rc = check_device(pl);
+  if (rc) return rc;
+  if (pl->chunk_len > 0 && (n_vis + pl->chunk_len - 1) / pl->chunk_len > 0x7FFFFFFFLL)
+    return fail(GRID_ERR_INVALID, "too many chunks");
+
+  Args a = make_args(pl, n_vis, uv);
+  a.vis = vis;
+  a.weights = weights;
+  a.table = kernel_table;
+  a.grid = (float2*)grid_out;
+  cudaError_t e;
+  if (pl->desc.schedule == GRID_SCHED_CHUNKED) {
+    const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
+    void* args[] = {&a};
+    e = cudaLaunchKernel(pl->k->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
+    return GRID_OK;
+  }
+  rc = ensure_patch_scratch(pl, a.n_chunks);
+  if (rc) return rc;
+  const PatchScratch& s = pl->ps;
+  e = launch_patch_binning(a, s, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "patch binning");
+  a.chunk_order = s.chunk_order;
+  a.work = s.work;
+  a.n_work = s.n_work;
+  a.work_next = s.work_next;
+  a.win = s.win;
+  long long blocks = (long long)pl->sm_count * pl->occ_grid;
+  const long long max_items = s.n_patches + a.n_chunks / s.max_chunks + 1;
+  if (blocks > max_items) blocks = max_items;
+  void* args[] = {&a};
+  e = cudaLaunchKernel(pl->k->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
+  return GRID_OK;
+}
+
+int degrid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* grid_in, const void* kernel_table, void* vis,
+           cudaStream_t stream) {
+  g_err.clear();
+  if (!pl) return fail(GRID_ERR_INVALID, "null plan");
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
+  if (!kernel_table || !grid_in) return fail(GRID_ERR_INVALID, "null kernel_table or grid");
+  if (!aligned(grid_in, 16)) return fail(GRID_ERR_INVALID, "grid must be 16-byte aligned");
+  if (n_vis == 0) return GRID_OK;
+  if (!uv || !vis) return fail(GRID_ERR_INVALID, "null uv or vis");
+  if (!aligned(uv, 16) || !aligned(vis, 8)) return fail(GRID_ERR_INVALID, "uv must be 16-byte and vis 8-byte aligned");
+  int rc = check_device(pl);
+  if (rc) return rc;
+  Args a = make_args(pl, n_vis, uv);
+  a.table = kernel_table;
+  a.grid = (float2*)grid_in;
+  a.vis_out = (float2*)vis;
+  const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(pl->k->degrid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_degrid, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "degrid kernel launch");
+  return GRID_OK;
+}
+
+int grid_make_kernel_table(int S, int oversample, double beta, int precision, void* table_out, cudaStream_t stream) {
+  g_err.clear();
+  if (S < 1 || S > 64 || !is_pow2(oversample) || oversample > 256) return fail(GRID_ERR_INVALID, "S=%d oversample=%d", S, oversample);
+  if (!(beta >= 0.0) || beta > 700.0) return fail(GRID_ERR_INVALID, "beta=%g out of range", beta);
+  if (precision < GRID_PREC_F32 || precision > GRID_PREC_F16) return fail(GRID_ERR_INVALID, "precision=%d", precision);
+  if (!table_out) return fail(GRID_ERR_INVALID, "null table_out");
+  cudaError_t e = launch_kb_table(S, oversample, beta, precision, table_out, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kb_table kernel launch");
+  return GRID_OK;
+}
+
+int grid_compute_indices(grid_plan_t pl, int64_t n_vis, const double* uv, int32_t* cell, int32_t* sub, cudaStream_t stream) {
+  g_err.clear();
+  if (!pl) return fail(GRID_ERR_INVALID, "null plan");
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis out of range");
+  if (n_vis == 0) return GRID_OK;
+  if (!uv || !cell || !sub) return fail(GRID_ERR_INVALID, "null pointer");
+  if (!aligned(uv, 16) || !aligned(cell, 8) || !aligned(sub, 8)) return fail(GRID_ERR_INVALID, "misaligned pointer");
+  int rc = check_device(pl);
+  if (rc) return rc;
+  Args a = make_args(pl, n_vis, uv);
+  cudaError_t e = launch_indices(a, cell, sub, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "indices kernel launch");
+  return GRID_OK;
+}
+
+int grid_plan_skipped(grid_plan_t pl, int64_t* n_skipped, int reset) {
+  if (!pl || !n_skipped) return fail(GRID_ERR_INVALID, "null argument");
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpy(&v, pl->d_skipped, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  *n_skipped = (int64_t)v;
+  if (reset) {
+    e = cudaMemset(pl->d_skipped, 0, sizeof v);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  }
+  return GRID_OK;
+}
+
+int grid_device_info(int* sm_count, int* fma_lanes_per_sm, int* max_clock_khz) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  int sms = 0, clk = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (sm_count) *sm_count = sms;
+  if (fma_lanes_per_sm) *fma_lanes_per_sm = 128;
+  if (max_clock_khz) *max_clock_khz = clk;
+  return GRID_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,38 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace gbg {
+
+struct PatchScratch {
+  int patch;        // patch side in cells
+  int n_pu;         // patches per grid axis
+  int n_patches;
+  int halo_lo;      // window origin = patch origin - halo_lo
+  int win;          // window side in cells
+  int max_chunks;   // chunks per work item
+  int max_work;
+  int* patch_count;
+  int* patch_off;
+  int* chunk_patch;
+  int* chunk_slot;
+  int* chunk_order;
+  int4* work;
+  int* n_work;
+  int* work_next;
+};
+
+// Kernel tables, one per polarization count (defined in inst_p*.cu).
+const KernelEntry* kernels_p1(int* n);
+const KernelEntry* kernels_p2(int* n);
+const KernelEntry* kernels_p4(int* n);
+
+cudaError_t launch_kb_table(int S, int O, double beta, int fmt, void* out, cudaStream_t st);
+cudaError_t launch_indices(const Args& a, int32_t* cell, int32_t* sub, cudaStream_t st);
+cudaError_t launch_patch_binning(const Args& a, const PatchScratch& ps, cudaStream_t st);
+
+}  // namespace gbg

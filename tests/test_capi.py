@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/gridder.h declares, and rejects bad arguments with
+GRID_ERR_INVALID before touching the device."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1605_07023_gb300 import _lib, build
+    if not os.path.exists(_lib.LIB_PATH):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("library not built and nvcc unavailable")
+        build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gridder.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("grid_plan_create", "grid", "degrid", "grid_make_kernel_table", "grid_compute_indices", "grid_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1605_07023_gb300 import _lib
+    names = declared_functions()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.EXPORTS)
+
+
+def test_invalid_plans_are_rejected_on_the_host(lib):
+    from paper_1605_07023_gb300 import _lib
+    h = ctypes.c_void_p()
+    bad = [(0, 7, 8, 1, 1), (255, 7, 8, 1, 1), (256, 0, 8, 1, 1), (256, 7, 6, 1, 1), (256, 7, 8, 3, 1),
+           (256, 7, 8, 1, 0), (256, 7, 8, 1, 9), (8, 9, 8, 1, 1), (65536, 7, 8, 1, 1), (256, 65, 8, 1, 1),
+           (256, 7, 512, 1, 1)]
+    for args in bad:
+        rc = lib.grid_plan_create(ctypes.byref(h), *args)
+        assert rc == _lib.GRID_ERR_INVALID, (args, rc)
+        assert lib.grid_last_error().decode()
+        assert not h.value
+
+
+def test_null_arguments(lib):
+    from paper_1605_07023_gb300 import _lib
+    assert lib.grid_plan_create(None, 256, 7, 8, 1, 1) == _lib.GRID_ERR_INVALID
+    assert lib.grid(None, 10, None, None, None, None, None, None) == _lib.GRID_ERR_INVALID
+    assert lib.degrid(None, 10, None, None, None, None, None) == _lib.GRID_ERR_INVALID
+    assert lib.grid_make_kernel_table(0, 8, 16.0, 0, None, None) == _lib.GRID_ERR_INVALID
+    assert lib.grid_make_kernel_table(7, 8, 16.0, 0, None, None) == _lib.GRID_ERR_INVALID
+    assert lib.grid_make_kernel_table(7, 8, float("nan"), 0, ctypes.c_void_p(16), None) == _lib.GRID_ERR_INVALID
+    lib.grid_plan_destroy(None)
+
+
+def test_desc_init_defaults(lib):
+    from paper_1605_07023_gb300 import _lib
+    d = _lib.GridPlanDesc()
+    lib.grid_plan_desc_init(ctypes.byref(d), 2048, 7, 8, 4, 2)
+    assert (d.G, d.S, d.oversample, d.npol, d.Bu, d.Bv) == (2048, 7, 8, 4, 2, 2)
+    assert d.precision == 0 and d.schedule == 0
