@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--degrid-config", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--vis", type=int, default=0, help="use only the first N visibilities (profiling runs)")
+    ap.add_argument("--skip-plain", action="store_true", help="do not time the plain Romein kernel (profiling runs)")
     return ap.parse_args()
 
 
@@ -73,23 +75,15 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
     import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1605_07023_gb300 import sharding
+    return sharding.reduce_max(x, "cuda" if torch.cuda.is_available() else "cpu") if world > 1 else x
 
 
 def sum_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
     import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    from paper_1605_07023_gb300 import sharding
+    return sharding.reduce_sum(x, "cuda" if torch.cuda.is_available() else "cpu") if world > 1 else x
 
 
 class ClockSampler:
@@ -173,7 +167,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     table64 = oracle.kb_table(w.S, w.oversample, w.beta).astype(np.float32).astype(np.float64)
-    n_sample = 250_000
+    n_sample = w.n_vis
     for _ in range(args.warmup):
         cpu_oracle_rate(w, 20_000, table64)
     rates, times = [], []
@@ -186,9 +180,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"first {n_sample} visibilities per step"},
+        "config": {"workload": WORKLOAD, "sample": "the whole batch per step (warm-up steps use 20,000 visibilities)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {n_sample} of 8,257,536 visibilities, grid + degrid, 1 thread"},
+                         "sample": f"all {n_sample} visibilities per step, grid + degrid, FP64, 1 thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -213,7 +207,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     # weak scaling: every rank grids its own observation (independent problems, different seed)
-    w = synth.quad_pol(seed=rank)
+    from paper_1605_07023_gb300 import sharding
+    w = synth.quad_pol(seed=sharding.rank_seed(0, rank))
+    if args.vis:
+        w = synth.scaled_down(w, args.vis)
     S2 = w.S * w.S
     stream = torch.cuda.current_stream()
 
@@ -280,8 +277,11 @@ def main():
     taps_all = sum_over_ranks(2.0 * n_valid * S2, world)
     value = taps_all * args.steps / (total_ms / 1e3)
 
-    # plain Romein (B=1, chunked, 1024 vis per team), same inputs, same clocks window
-    p_total, p_g, p_d = timed(pplan, pplan, args.steps, args.warmup)
+    # plain Romein (B=1, chunked, 1024 vis per team), same inputs
+    if args.skip_plain:
+        p_total, p_g, p_d = float("nan"), float("nan"), float("nan")
+    else:
+        p_total, p_g, p_d = timed(pplan, pplan, args.steps, args.warmup)
     p_value = 2.0 * n_valid * S2 / (p_total / args.steps / 1e3)
 
     info = gb.device_info()
@@ -339,10 +339,14 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         table64 = table.cpu().numpy().astype(np.float64)
-        n_sample = 500_000
-        r, dt = cpu_oracle_rate(w, n_sample, table64)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_sample} of 8,257,536 visibilities, grid + degrid, FP64, 1 thread ({dt:.1f} s)"}
+        # the whole batch, repeated until about 10 s of CPU work
+        rates, spent = [], 0.0
+        while spent < 10.0 and len(rates) < 4:
+            r, dt = cpu_oracle_rate(w, w.n_vis, table64)
+            rates.append(r)
+            spent += dt
+        cpu = {"value": float(np.mean(rates)), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"all {w.n_vis} visibilities x {len(rates)}, grid + degrid, FP64, 1 thread ({spent:.1f} s)"}
 
     launches_per_step = (4 if best_grid["schedule"] == "patch" else 1) + 1
     if rank == 0:

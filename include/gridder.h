@@ -129,6 +129,17 @@ int degrid(grid_plan_t plan, int64_t n_vis, const double* uv, const void* grid, 
            void* vis, cudaStream_t stream);
 
 /*
+ * Weighted degridding, the exact adjoint of grid() with weights w:
+ *   vis[n][p] = w_n * sum_{i,j} table[r_u][i] * table[r_v][j] * grid[p][C_v-h+j][C_u-h+i]
+ * This is the backward pass of grid() with respect to the visibilities
+ * (Sec. 2.2 defines the forward map). weights may be NULL, which gives
+ * degrid(). The other arguments and the overwrite semantics are those of
+ * degrid().
+ */
+int degrid_weighted(grid_plan_t plan, int64_t n_vis, const double* uv, const void* grid, const void* kernel_table,
+                    const float* weights, void* vis, cudaStream_t stream);
+
+/*
  * Oversampled Kaiser-Bessel table (Sec. 2.2: precomputed and oversampled).
  * Writes [O][S] values to the DEVICE buffer table_out, in the plan precision
  * `precision`:

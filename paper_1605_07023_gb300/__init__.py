@@ -20,7 +20,7 @@ import ctypes
 from . import _lib
 from ._lib import GridderError, PREC, SCHED
 
-__all__ = ["Plan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "grid_make_kernel_table",
+__all__ = ["Plan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "degrid_weighted", "grid_make_kernel_table",
            "grid_compute_indices", "device_info", "GridderError"]
 
 
@@ -145,6 +145,11 @@ def grid(plan: Plan, uv, vis, weights, kernel_table, grid_out, stream=None):
 
 def degrid(plan: Plan, uv, grid_in, kernel_table, vis_out=None, stream=None):
     """degrid(): visibilities [n, P] complex64 from grid_in (overwrites vis_out). Returns vis_out."""
+    return degrid_weighted(plan, uv, grid_in, kernel_table, None, vis_out, stream)
+
+
+def degrid_weighted(plan: Plan, uv, grid_in, kernel_table, weights, vis_out=None, stream=None):
+    """degrid_weighted(): w_n * degrid(grid_in)[n], the adjoint of weighted grid(). weights None = degrid()."""
     torch = _torch()
     n = uv.shape[0]
     if vis_out is None:
@@ -153,9 +158,12 @@ def degrid(plan: Plan, uv, grid_in, kernel_table, vis_out=None, stream=None):
     pg = _dptr(grid_in, "grid", torch.complex64, 3)
     pt = _dptr(kernel_table, "kernel_table", (torch.float32, torch.bfloat16, torch.float16), 2)
     po = _dptr(vis_out, "vis", torch.complex64, 2)
+    pw = _dptr(weights, "weights", torch.float32, 1)
     if tuple(grid_in.shape) != (plan.npol, plan.G, plan.G):
         raise ValueError(f"grid must be [{plan.npol}, {plan.G}, {plan.G}]")
-    _lib.check(_lib.load().degrid(plan.handle, n, pu, pg, pt, po, _stream_ptr(stream)))
+    if weights is not None and weights.shape[0] != n:
+        raise ValueError("weights must have one entry per visibility")
+    _lib.check(_lib.load().degrid_weighted(plan.handle, n, pu, pg, pt, pw or None, po, _stream_ptr(stream)))
     return vis_out
 
 

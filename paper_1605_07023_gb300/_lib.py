@@ -21,7 +21,7 @@ PREC = {"f32": 0, "bf16": 1, "f16": 2}
 SCHED = {"chunked": 0, "patch": 1}
 
 EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
-           "grid", "degrid", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
+           "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
            "grid_last_error", "grid_device_info")
 
 
@@ -65,6 +65,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid.restype = i32
     lib.degrid.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.degrid.restype = i32
+    lib.degrid_weighted.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    lib.degrid_weighted.restype = i32
     lib.grid_make_kernel_table.argtypes = [i32, i32, ctypes.c_double, i32, vp, vp]
     lib.grid_make_kernel_table.restype = i32
     lib.grid_compute_indices.argtypes = [vp, i64, vp, vp, vp, vp]

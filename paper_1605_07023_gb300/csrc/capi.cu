@@ -63,7 +63,7 @@ size_t tables_bytes(const Geometry& g, int bu, int bv) {
 size_t grid_smem(const Geometry& g, int bu, int bv, int win) {
   size_t s = tables_bytes(g, bu, bv) + 2 * (size_t)g.tpc * kRB * (16 + 8 * g.P);
   s = a16(s);
-  if (win > 0) s += (size_t)g.P * win * win * 8;
+  if (win > 0) s += a16((size_t)g.P * win * (2 * win + 1) * 4);
   return s;
 }
 
@@ -236,12 +236,15 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   }
   pl->smem_grid = grid_smem(g, d.Bu, d.Bv, win);
   pl->smem_degrid = degrid_smem(g, d.Bu, d.Bv);
-  if (pl->smem_grid > smem_max || pl->smem_degrid > smem_max) {
+  if (pl->smem_grid + fa_g.sharedSizeBytes > smem_max || pl->smem_degrid + fa_d.sharedSizeBytes > smem_max) {
     delete pl;
     return fail(GRID_ERR_UNSUPPORTED, "kernel needs more shared memory than the device offers");
   }
-  e = cudaFuncSetAttribute(k->grid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_grid);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k->degrid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_degrid);
+  // Kernels are shared by every plan with the same (Bu, Bv, P), so each one's dynamic shared
+  // memory limit is raised to the device maximum once, not to this plan's need.
+  e = cudaFuncSetAttribute(k->grid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_g.sharedSizeBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k->degrid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_d.sharedSizeBytes));
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute"); }
   if (d.schedule == GRID_SCHED_PATCH) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occ_grid, k->grid_fn, pl->threads, pl->smem_grid);
@@ -325,6 +328,11 @@ int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const
 
 int degrid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* grid_in, const void* kernel_table, void* vis,
            cudaStream_t stream) {
+  return degrid_weighted(pl, n_vis, uv, grid_in, kernel_table, nullptr, vis, stream);
+}
+
+int degrid_weighted(grid_plan_t pl, int64_t n_vis, const double* uv, const void* grid_in, const void* kernel_table,
+                    const float* weights, void* vis, cudaStream_t stream) {
   g_err.clear();
   if (!pl) return fail(GRID_ERR_INVALID, "null plan");
   if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
@@ -333,9 +341,11 @@ int degrid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* grid_in,
   if (n_vis == 0) return GRID_OK;
   if (!uv || !vis) return fail(GRID_ERR_INVALID, "null uv or vis");
   if (!aligned(uv, 16) || !aligned(vis, 8)) return fail(GRID_ERR_INVALID, "uv must be 16-byte and vis 8-byte aligned");
+  if (weights && !aligned(weights, 4)) return fail(GRID_ERR_INVALID, "weights must be 4-byte aligned");
   int rc = check_device(pl);
   if (rc) return rc;
   Args a = make_args(pl, n_vis, uv);
+  a.weights = weights;
   a.table = kernel_table;
   a.grid = (float2*)grid_in;
   a.vis_out = (float2*)vis;

@@ -247,14 +247,19 @@ __device__ __forceinline__ void flush_global(float2 (&acc)[P][BV][BU], unsigned 
 }
 
 // Shared-memory patch flush: the block lies inside the CTA's window
-// [wu0, wu0+win) x [wv0, wv0+win). Window layout: [P][win][win] float2.
+// [wu0, wu0+win) x [wv0, wv0+win). Window layout: [P][win] rows of
+// win_stride(win) = 2*win + 1 floats (interleaved re, im). The odd stride
+// puts the rows that different threads flush at once in different banks.
+__host__ __device__ inline int win_stride(int win) { return 2 * win + 1; }
+
 template <int BU, int BV, int P>
 __device__ __forceinline__ void flush_window(float2 (&acc)[P][BV][BU], int lu, int lv, float* __restrict__ win_buf, int win) {
+  const int ws = win_stride(win);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
 #pragma unroll
     for (int j = 0; j < BV; ++j) {
-      float* row = win_buf + 2 * (((size_t)p * win + lv + j) * win + lu);
+      float* row = win_buf + ((size_t)p * win + lv + j) * ws + 2 * lu;
 #pragma unroll
       for (int i = 0; i < BU; ++i) {
         const float2 q = acc[p][j][i];
@@ -428,12 +433,13 @@ __global__ void grid_kernel(Args a) {
   // ---- patch schedule
   __shared__ int s_item;
   const int win = a.win;
-  const size_t win_floats = (size_t)P * win * win * 2;
+  const int ws = win_stride(win);
+  const int win_floats = P * win * ws;
   const int n_work = *a.n_work;
   for (;;) {
     __syncthreads();  // previous item fully flushed; tables ready on the first pass
     if (threadIdx.x == 0) s_item = atomicAdd(a.work_next, 1);
-    for (size_t i = threadIdx.x; i < win_floats / 4; i += blockDim.x) ((float4*)win_buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < win_floats; i += blockDim.x) win_buf[i] = 0.f;
     __syncthreads();
     const int item = s_item;
     if (item >= n_work) break;
@@ -470,7 +476,7 @@ __global__ void grid_kernel(Args a) {
     }
     __syncthreads();
     // add the window to the grid: coalesced float4 atomics, all-zero vectors skipped
-    const int rowf4 = win / 2;  // float4 per window row (win even)
+    const int rowf4 = win / 2;  // float4 (two cells) per window row (win even)
     const int total = P * win * rowf4;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
       const int c4 = i % rowf4;
@@ -478,7 +484,8 @@ __global__ void grid_kernel(Args a) {
       const int vv = rowi % win;
       const int p = rowi / win;
       const int gu = wu0 + 2 * c4, gv = wv0 + vv;
-      const float4 q = ((const float4*)win_buf)[i];
+      const float* src = win_buf + (size_t)rowi * ws + 4 * c4;
+      const float4 q = make_float4(src[0], src[1], src[2], src[3]);
       const bool nz = (q.x != 0.f) | (q.y != 0.f) | (q.z != 0.f) | (q.w != 0.f);
       if (nz && gu >= 0 && gv >= 0 && gu + 1 < g.G && gv < g.G)
         atomicAdd((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
@@ -617,6 +624,7 @@ __global__ void degrid_kernel(Args a) {
           const float* col = red + (size_t)o * tsp;
           float sum = 0.f;
           for (int t = 0; t < g.ts; ++t) sum += col[t];
+          if (a.weights) sum *= a.weights[k];
           ((float*)a.vis_out)[k * 2 * P + (o - r * 2 * P)] = sum;
         }
       }

@@ -191,6 +191,18 @@ def test_grid_empty_and_single(gb):
     check_grid(gb, w, 1, 1, "patch")
 
 
+def test_plans_sharing_a_kernel_do_not_interfere(gb):
+    """A patch plan still launches after a chunked plan with the same (Bu, Bv, P) was created."""
+    w = synth.scaled_down(quad_pol(), 30_000)
+    table32 = kb32(w.S, w.oversample)
+    p_patch = gb.Plan(w.G, w.S, w.oversample, 4, B=2, schedule="patch")
+    p_chunk = gb.Plan(w.G, w.S, w.oversample, 4, B=2, schedule="chunked")
+    ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, table32)
+    for plan in (p_patch, p_chunk, p_patch):
+        got = run_grid(gb, w, plan, table32)
+        assert max(rel_l2(got[p], ref[p]) for p in range(4)) <= TOL
+
+
 def test_grid_accumulates(gb):
     """grid() adds to what is already in the grid."""
     w = synth.plain_single_pol()
