@@ -338,7 +338,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        table64 = table.cpu().numpy().astype(np.float64)
+        oracle.build()
+        table64 = oracle.kb_table(w.S, w.oversample, w.beta)
         # the whole batch, repeated until about 10 s of CPU work
         rates, spent = [], 0.0
         while spent < 10.0 and len(rates) < 4:

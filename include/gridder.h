@@ -165,6 +165,46 @@ int grid_compute_indices(grid_plan_t plan, int64_t n_vis, const double* uv, int3
  */
 int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
 
+/*
+ * Batched gridding (NEXT-2 in the design notes): many grids of the same side
+ * G, oversampling O and polarization count, for example every
+ * (channel, w-plane) of an observation (Sec. 5 grids each w-slice with its
+ * own kernel instance). Each item has its own visibilities, GCF support S
+ * (<= max_S), kernel table and grid. One persistent kernel launch grids all
+ * of them. Work units (runs of chunks of one item) are ordered by cost on
+ * the host, and CTAs take them from an atomic counter. Every item uses the
+ * gridding semantics of grid(), including accumulation into its grid.
+ *
+ * grid_batch_create(): a plan for the common parameters and the block shape
+ *   (Bu, Bv). vis_per_chunk and threads may be 0 (defaults 256 and 256).
+ * grid_batch_set(): uploads the item descriptors and the unit list
+ *   (synchronous). `items` is a host array. The pointers inside it are device
+ *   pointers, borrowed until the last execute using them has completed.
+ * grid_batch_execute(): enqueues a counter reset and ONE kernel launch on
+ *   `stream`. It allocates nothing and does not synchronise, so it can be
+ *   captured in a CUDA graph and replayed.
+ */
+typedef struct grid_batch_s* grid_batch_t;
+
+typedef struct {
+  int64_t n_vis;
+  const double* uv;          /* [n_vis][2] */
+  const void* vis;           /* [n_vis][npol] complex, in the batch precision */
+  const float* weights;      /* [n_vis] or NULL */
+  const void* kernel_table;  /* [O][S] */
+  void* grid;                /* [npol][G][G] complex64 */
+  int S;
+} grid_batch_item;
+
+int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu, int Bv, int max_S, int precision,
+                      int vis_per_chunk, int threads);
+int grid_batch_set(grid_batch_t batch, int n_items, const grid_batch_item* items);
+int grid_batch_execute(grid_batch_t batch, cudaStream_t stream);
+int grid_batch_skipped(grid_batch_t batch, int64_t* n_skipped, int reset);
+int grid_batch_describe(grid_batch_t batch, int* threads, int* n_units, int* ctas);
+void grid_batch_destroy(grid_batch_t batch);
+const char* grid_batch_last_error(void);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* grid_last_error(void);
 

@@ -20,7 +20,7 @@ import ctypes
 from . import _lib
 from ._lib import GridderError, PREC, SCHED
 
-__all__ = ["Plan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "degrid_weighted", "grid_make_kernel_table",
+__all__ = ["Plan", "BatchPlan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "degrid_weighted", "grid_make_kernel_table",
            "grid_compute_indices", "device_info", "GridderError"]
 
 
@@ -192,3 +192,74 @@ def device_info() -> dict:
     sms, lanes, clk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _lib.check(_lib.load().grid_device_info(ctypes.byref(sms), ctypes.byref(lanes), ctypes.byref(clk)))
     return dict(sm_count=sms.value, fma_lanes_per_sm=lanes.value, max_clock_khz=clk.value)
+
+
+class BatchPlan:
+    """Batched gridding of many grids in one persistent launch (grid_batch_* in the C ABI).
+
+    items: list of dicts with keys uv, vis, weights (or None), table, grid, S,
+    all CUDA tensors (see grid()). Tensors must stay alive while the batch is
+    executed. execute() enqueues one kernel on the current stream and can be
+    captured in a CUDA graph.
+    """
+
+    def __init__(self, G: int, oversample: int, npol: int, Bu: int = 2, Bv: int = 2, max_S: int = 15,
+                 precision: str = "f32", vis_per_chunk: int = 0, threads: int = 0):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(lib.grid_batch_create(ctypes.byref(h), G, oversample, npol, Bu, Bv, max_S, PREC[precision],
+                                         vis_per_chunk, threads), batch=True)
+        self._h = h
+        self.G, self.oversample, self.npol, self.precision = G, oversample, npol, precision
+        self._keep = []
+
+    def set(self, items) -> None:
+        torch = _torch()
+        arr = (_lib.GridBatchItem * max(1, len(items)))()
+        keep = []
+        for k, it in enumerate(items):
+            n = it["uv"].shape[0]
+            arr[k].n_vis = n
+            arr[k].uv = _dptr(it["uv"], "uv", torch.float64, 2) or None
+            arr[k].vis = _dptr(it["vis"], "vis", _vis_dtype(self)) or None
+            arr[k].weights = _dptr(it.get("weights"), "weights", torch.float32, 1) or None
+            arr[k].kernel_table = _dptr(it["table"], "kernel_table", (torch.float32, torch.bfloat16, torch.float16), 2) or None
+            g = it["grid"]
+            if tuple(g.shape) != (self.npol, self.G, self.G):
+                raise ValueError("each grid must be [P, G, G]")
+            arr[k].grid = _dptr(g, "grid", torch.complex64, 3) or None
+            arr[k].S = int(it["S"])
+            keep.append(it)
+        _lib.check(_lib.load().grid_batch_set(self.handle, len(items), arr), batch=True)
+        self._keep = keep
+
+    def execute(self, stream=None) -> None:
+        _lib.check(_lib.load().grid_batch_execute(self.handle, _stream_ptr(stream)), batch=True)
+
+    def describe(self) -> dict:
+        t, u, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(_lib.load().grid_batch_describe(self.handle, ctypes.byref(t), ctypes.byref(u), ctypes.byref(c)),
+                   batch=True)
+        return dict(threads=t.value, units=u.value, ctas=c.value)
+
+    def skipped(self, reset: bool = False) -> int:
+        v = ctypes.c_int64()
+        _lib.check(_lib.load().grid_batch_skipped(self.handle, ctypes.byref(v), int(reset)), batch=True)
+        return v.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("batch plan is closed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib.load().grid_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,7 +22,14 @@ SCHED = {"chunked": 0, "patch": 1}
 
 EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
-           "grid_last_error", "grid_device_info")
+           "grid_last_error", "grid_device_info", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
+           "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error")
+
+
+class GridBatchItem(ctypes.Structure):
+    _fields_ = [("n_vis", ctypes.c_int64), ("uv", ctypes.c_void_p), ("vis", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("kernel_table", ctypes.c_void_p), ("grid", ctypes.c_void_p),
+                ("S", ctypes.c_int)]
 
 
 class GridPlanDesc(ctypes.Structure):
@@ -77,11 +84,26 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid_last_error.restype = ctypes.c_char_p
     lib.grid_device_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.grid_device_info.restype = i32
+    lib.grid_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, i32, i32, i32]
+    lib.grid_batch_create.restype = i32
+    lib.grid_batch_set.argtypes = [vp, i32, ctypes.POINTER(GridBatchItem)]
+    lib.grid_batch_set.restype = i32
+    lib.grid_batch_execute.argtypes = [vp, vp]
+    lib.grid_batch_execute.restype = i32
+    lib.grid_batch_skipped.argtypes = [vp, ctypes.POINTER(i64), i32]
+    lib.grid_batch_skipped.restype = i32
+    lib.grid_batch_describe.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.grid_batch_describe.restype = i32
+    lib.grid_batch_destroy.argtypes = [vp]
+    lib.grid_batch_destroy.restype = None
+    lib.grid_batch_last_error.argtypes = []
+    lib.grid_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
 
-def check(rc: int) -> None:
+def check(rc: int, batch: bool = False) -> None:
     if rc != GRID_OK:
-        msg = load().grid_last_error().decode(errors="replace")
+        lib = load()
+        msg = (lib.grid_batch_last_error() if batch else lib.grid_last_error()).decode(errors="replace")
         raise GridderError(rc, msg)

@@ -18,9 +18,11 @@ struct grid_plan_s {
   int threads;          // threads per CTA (tpc * ts)
   int chunk_len;
   const KernelEntry* k;
+  const void* grid_fn;  // gridding kernel of the plan's schedule
   size_t smem_grid;     // dynamic shared memory of the gridding kernel
   size_t smem_degrid;
   int occ_grid;         // resident gridding CTAs per SM (patch schedule)
+  int warp_sync;        // team size divides 32: teams synchronise per warp
   unsigned long long* d_skipped;
   PatchScratch ps;
   long long ps_chunks_cap;  // chunk capacity of the patch scratch
@@ -58,18 +60,6 @@ const KernelEntry* find_kernel(int bu, int bv, int p) {
 
 size_t tables_bytes(const Geometry& g, int bu, int bv) {
   return a16((size_t)g.O * bu * g.nbu * 4) + a16((size_t)g.O * bv * g.nbv * 4);
-}
-
-size_t grid_smem(const Geometry& g, int bu, int bv, int win) {
-  size_t s = tables_bytes(g, bu, bv) + 2 * (size_t)g.tpc * kRB * (16 + 8 * g.P);
-  s = a16(s);
-  if (win > 0) s += a16((size_t)g.P * win * (2 * win + 1) * 4);
-  return s;
-}
-
-size_t degrid_smem(const Geometry& g, int bu, int bv) {
-  const int tsp = g.ts | 1;
-  return tables_bytes(g, bu, bv) + (size_t)g.tpc * kRBD * 16 + a16((size_t)g.tpc * kRBD * 2 * g.P * tsp * 4);
 }
 
 void free_patch(grid_plan_s* pl) {
@@ -118,6 +108,7 @@ Args make_args(const grid_plan_s* pl, int64_t n_vis, const double* uv) {
   a.skipped = pl->d_skipped;
   a.vis_fmt = pl->desc.precision;
   a.tab_fmt = pl->desc.precision;
+  a.warp_sync = pl->warp_sync;
   return a;
 }
 
@@ -182,8 +173,9 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   e = cudaGetDeviceProperties(&prop, pl->device);
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDeviceProperties"); }
   pl->sm_count = prop.multiProcessorCount;
+  pl->grid_fn = d.schedule == GRID_SCHED_PATCH ? k->grid_patch_fn : k->grid_fn;
   cudaFuncAttributes fa_g, fa_d;
-  e = cudaFuncGetAttributes(&fa_g, k->grid_fn);
+  e = cudaFuncGetAttributes(&fa_g, pl->grid_fn);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa_d, k->degrid_fn);
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncGetAttributes (is this an sm_103 GPU?)"); }
   const int max_thr = fa_g.maxThreadsPerBlock < fa_d.maxThreadsPerBlock ? fa_g.maxThreadsPerBlock : fa_d.maxThreadsPerBlock;
@@ -192,13 +184,14 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     delete pl;
     return fail(GRID_ERR_UNSUPPORTED, "team of %d threads exceeds the %d threads per CTA this kernel can run", ts, max_thr);
   }
-  const int target = d.threads > 0 ? d.threads : 256;
+  const int target = d.threads > 0 ? d.threads : (d.schedule == GRID_SCHED_PATCH ? 384 : 256);
   g.tpc = target / g.ts;
   if (g.tpc < 1) g.tpc = 1;
   while (g.tpc > 1 && g.tpc * g.ts > max_thr) --g.tpc;
   pl->threads = g.tpc * g.ts;
+  pl->warp_sync = (g.ts <= 32 && 32 % g.ts == 0) ? 1 : 0;
 
-  if (d.vis_per_chunk == 0) d.vis_per_chunk = d.schedule == GRID_SCHED_PATCH ? 64 : 1024;
+  if (d.vis_per_chunk == 0) d.vis_per_chunk = d.schedule == GRID_SCHED_PATCH ? 64 : 256;
   pl->chunk_len = d.vis_per_chunk;
 
   const size_t tb = tables_bytes(g, d.Bu, d.Bv);
@@ -213,16 +206,16 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     PatchScratch& s = pl->ps;
     int patch = d.patch;
     const int halo = 12;
-    if (patch <= 0) patch = d.npol == 4 ? 32 : d.npol == 2 ? 64 : 96;
+    if (patch <= 0) patch = d.npol == 4 ? 32 : d.npol == 2 ? 48 : 96;
     patch = (patch + 1) & ~1;  // even, so window rows start on 16-byte boundaries
     // shrink the patch until the window fits next to the tables and records
     for (;;) {
       win = patch + 2 * halo + (g.nbu > g.nbv ? g.nbu : g.nbv);
-      win = (win + 1) & ~1;
-      if (grid_smem(g, d.Bu, d.Bv, win) + 1024 <= smem_max || patch <= 8) break;
+      win = (win + 15) & ~15;  // a multiple of 16 (bank-conflict-free strides)
+      if (k->grid_smem(g, pl->threads, win) + fa_g.sharedSizeBytes + 1024 <= smem_max || patch <= 8) break;
       patch -= 8;
     }
-    if (patch < 1 || grid_smem(g, d.Bu, d.Bv, win) + 1024 > smem_max) {
+    if (patch < 1 || k->grid_smem(g, pl->threads, win) + fa_g.sharedSizeBytes + 1024 > smem_max) {
       delete pl;
       return fail(GRID_ERR_UNSUPPORTED, "patch window does not fit in shared memory");
     }
@@ -234,20 +227,20 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     s.win = win;
     s.max_chunks = 128;
   }
-  pl->smem_grid = grid_smem(g, d.Bu, d.Bv, win);
-  pl->smem_degrid = degrid_smem(g, d.Bu, d.Bv);
+  pl->smem_grid = k->grid_smem(g, pl->threads, win);
+  pl->smem_degrid = k->degrid_smem(g, pl->threads, 0);
   if (pl->smem_grid + fa_g.sharedSizeBytes > smem_max || pl->smem_degrid + fa_d.sharedSizeBytes > smem_max) {
     delete pl;
     return fail(GRID_ERR_UNSUPPORTED, "kernel needs more shared memory than the device offers");
   }
   // Kernels are shared by every plan with the same (Bu, Bv, P), so each one's dynamic shared
   // memory limit is raised to the device maximum once, not to this plan's need.
-  e = cudaFuncSetAttribute(k->grid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_g.sharedSizeBytes));
+  e = cudaFuncSetAttribute(pl->grid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_g.sharedSizeBytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k->degrid_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_d.sharedSizeBytes));
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute"); }
   if (d.schedule == GRID_SCHED_PATCH) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occ_grid, k->grid_fn, pl->threads, pl->smem_grid);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occ_grid, pl->grid_fn, pl->threads, pl->smem_grid);
     if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
     if (pl->occ_grid < 1) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "gridding kernel cannot be resident with this shape"); }
   }
@@ -303,7 +296,7 @@ int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const
   if (pl->desc.schedule == GRID_SCHED_CHUNKED) {
     const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
     void* args[] = {&a};
-    e = cudaLaunchKernel(pl->k->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
+    e = cudaLaunchKernel(pl->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
     return GRID_OK;
   }
@@ -321,7 +314,7 @@ int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const
   const long long max_items = s.n_patches + a.n_chunks / s.max_chunks + 1;
   if (blocks > max_items) blocks = max_items;
   void* args[] = {&a};
-  e = cudaLaunchKernel(pl->k->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
+  e = cudaLaunchKernel(pl->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
   if (e != cudaSuccess) return cuda_fail(e, "grid kernel launch");
   return GRID_OK;
 }

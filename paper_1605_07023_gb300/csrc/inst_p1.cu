@@ -4,7 +4,10 @@
 
 namespace gbg {
 
-#define GB_ENTRY(BU, BV) {BU, BV, 1, (const void*)&grid_kernel<BU, BV, 1>, (const void*)&degrid_kernel<BU, BV, 1>}
+#define GB_ENTRY(BU, BV)                                                                                  \
+  {BU, BV, 1, (const void*)&grid_kernel<BU, BV, 1, false>, (const void*)&grid_kernel<BU, BV, 1, true>, \
+   (const void*)&degrid_kernel<BU, BV, 1>, &grid_smem_bytes<BU, BV, 1>, \
+   &degrid_smem_bytes<BU, BV, 1>}
 
 const KernelEntry* kernels_p1(int* n) {
   static const KernelEntry t[] = {

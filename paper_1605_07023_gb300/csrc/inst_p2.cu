@@ -4,7 +4,10 @@
 
 namespace gbg {
 
-#define GB_ENTRY(BU, BV) {BU, BV, 2, (const void*)&grid_kernel<BU, BV, 2>, (const void*)&degrid_kernel<BU, BV, 2>}
+#define GB_ENTRY(BU, BV)                                                                                  \
+  {BU, BV, 2, (const void*)&grid_kernel<BU, BV, 2, false>, (const void*)&grid_kernel<BU, BV, 2, true>, \
+   (const void*)&degrid_kernel<BU, BV, 2>, &grid_smem_bytes<BU, BV, 2>, \
+   &degrid_smem_bytes<BU, BV, 2>}
 
 const KernelEntry* kernels_p2(int* n) {
   static const KernelEntry t[] = {

@@ -4,7 +4,10 @@
 
 namespace gbg {
 
-#define GB_ENTRY(BU, BV) {BU, BV, 4, (const void*)&grid_kernel<BU, BV, 4>, (const void*)&degrid_kernel<BU, BV, 4>}
+#define GB_ENTRY(BU, BV)                                                                                  \
+  {BU, BV, 4, (const void*)&grid_kernel<BU, BV, 4, false>, (const void*)&grid_kernel<BU, BV, 4, true>, \
+   (const void*)&degrid_kernel<BU, BV, 4>, &grid_smem_bytes<BU, BV, 4>, \
+   &degrid_smem_bytes<BU, BV, 4>}
 
 const KernelEntry* kernels_p4(int* n) {
   static const KernelEntry t[] = {

@@ -37,6 +37,7 @@ namespace gbg {
 constexpr unsigned kInvalid = 0xFFFFFFFFu;
 constexpr int kRB = 16;   // records per team per staged batch (gridding)
 constexpr int kRBD = 8;   // records per team per batch (degridding; bounded by the reduction buffer)
+constexpr int kSlots = 8; // flush slots per warp (lanes parked per cooperative-flush round)
 
 enum { FMT_F32 = 0, FMT_BF16 = 1, FMT_F16 = 2 };
 
@@ -66,6 +67,7 @@ struct Args {
   const int* n_work;      // device count of work items
   int* work_next;         // device work counter (persistent CTAs)
   int win;                // patch window side in cells (patch + halo); 0 = chunked schedule
+  int warp_sync;          // 1: every team lies inside one warp (team size divides 32), teams sync per warp
   unsigned long long* skipped;
 };
 
@@ -211,6 +213,62 @@ __device__ __forceinline__ void load_taps(const float* p, float (&t)[B]) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory layouts (computed identically on host and device).
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Patch window: P planes of `win` rows; a row holds `win` complex cells as
+// interleaved (re, im) floats. win is a multiple of 16, so the row stride
+// 2*win + 4 is 4 (mod 32) floats and the plane stride is 8 (mod 32) floats:
+// the 2 x 2 cells x 4 polarizations of one block, flushed by one warp
+// instruction, fall in 32 different banks. Rows start on 16-byte boundaries.
+__host__ __device__ inline int win_row_stride(int win) { return 2 * win + 4; }
+__host__ __device__ inline int win_plane_stride(int win) {
+  const int x = win * win_row_stride(win);
+  return x + ((8 - x % 32) + 32) % 32;
+}
+
+struct SmemLayout {
+  size_t tabU, tabV, meta, vals, win, slots, keys, red, total;
+};
+
+template <int BU, int BV, int P>
+__host__ __device__ inline SmemLayout grid_layout(const Geometry& g, int nthreads, int win) {
+  SmemLayout L{};
+  size_t off = 0;
+  L.tabU = off; off += align16((size_t)g.O * BU * g.nbu * 4);
+  L.tabV = off; off += align16((size_t)g.O * BV * g.nbv * 4);
+  L.meta = off; off += align16((size_t)2 * g.tpc * kRB * 16);
+  L.vals = off; off += align16((size_t)2 * g.tpc * kRB * P * 8);
+  if (win > 0) {
+    const int nw = (nthreads + 31) / 32;
+    L.win = off; off += align16((size_t)P * win_plane_stride(win) * 4);
+    L.slots = off; off += align16((size_t)nw * kSlots * 2 * P * BU * BV * 4);
+    L.keys = off; off += align16((size_t)nw * kSlots * 4);
+  }
+  L.total = off;
+  return L;
+}
+
+template <int BU, int BV, int P>
+__host__ __device__ inline SmemLayout degrid_layout(const Geometry& g, int nthreads, int win) {
+  SmemLayout L{};
+  size_t off = 0;
+  const int tsp = g.ts | 1;
+  L.tabU = off; off += align16((size_t)g.O * BU * g.nbu * 4);
+  L.tabV = off; off += align16((size_t)g.O * BV * g.nbv * 4);
+  L.meta = off; off += align16((size_t)2 * g.tpc * kRBD * 16);
+  L.red = off; off += align16((size_t)g.tpc * kRBD * 2 * P * tsp * 4);
+  (void)nthreads;
+  (void)win;
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Flushes.
+
 // Flush one block of register accumulators to the grid in global memory with
 // vector atomic adds, then zero them. Cells past the grid's high edge (the
 // box can overhang it) hold exact zeros and are not written. All-zero
@@ -246,103 +304,107 @@ __device__ __forceinline__ void flush_global(float2 (&acc)[P][BV][BU], unsigned 
   }
 }
 
-// Shared-memory patch flush: the block lies inside the CTA's window
-// [wu0, wu0+win) x [wv0, wv0+win). Window layout: [P][win] rows of
-// win_stride(win) = 2*win + 1 floats (interleaved re, im). The odd stride
-// puts the rows that different threads flush at once in different banks.
-__host__ __device__ inline int win_stride(int win) { return 2 * win + 1; }
+struct WindowCtx {
+  float* buf;        // shared window
+  int win, ws, ps;   // side, row stride, plane stride (floats)
+  int wu0, wv0;      // grid cell of window (0, 0)
+  float* slots;      // this warp's flush slots
+  unsigned* keys;    // this warp's slot keys
+  unsigned wmask;    // lanes of this warp that exist
+};
 
+// Cooperative flush into the shared window. Each lane with need=true owns a
+// block (key) whose accumulators must be added. Blocks outside the window go
+// straight to global memory from their owner. The others are parked in the
+// warp's slots, kSlots at a time. Then all 32 lanes add them element by
+// element, so every shared atomic instruction runs with all lanes active
+// (the cost of a shared atomic is per instruction, not per active lane).
+// Must be called by every lane of the warp (warp-uniform).
 template <int BU, int BV, int P>
-__device__ __forceinline__ void flush_window(float2 (&acc)[P][BV][BU], int lu, int lv, float* __restrict__ win_buf, int win) {
-  const int ws = win_stride(win);
+__device__ __forceinline__ void window_flush(bool need, unsigned key, float2 (&acc)[P][BV][BU], float2* grid, int G,
+                                             const WindowCtx& w, int4& dirty) {
+  constexpr int F = 2 * P * BU * BV;
+  if (need) {
+    const int lu = (int)(key & 0xFFFFu) * BU - w.wu0;
+    const int lv = (int)(key >> 16) * BV - w.wv0;
+    if (lu < 0 || lv < 0 || lu + BU > w.win || lv + BV > w.win) {
+      flush_global<BU, BV, P>(acc, key, grid, G);
+      need = false;
+    } else {
+      dirty.x = min(dirty.x, lu);
+      dirty.y = min(dirty.y, lv);
+      dirty.z = max(dirty.z, lu + BU);
+      dirty.w = max(dirty.w, lv + BV);
+    }
+  }
+  unsigned m = __ballot_sync(w.wmask, need);
+  const int lane = threadIdx.x & 31;
+  while (m) {
+    unsigned take = 0, mm = m;
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
+    for (int k = 0; k < kSlots; ++k) {
+      const unsigned b = mm & (0u - mm);
+      take |= b;
+      mm &= ~b;
+    }
+    const int cnt = __popc(take);
+    if ((take >> lane) & 1u) {
+      const int rank = __popc(take & ((1u << lane) - 1u));
+      float* dst = w.slots + rank * F;
+      if constexpr (BU % 2 == 0) {
+        // slot base is 16-byte aligned (kSlots * F floats per warp, F even) and
+        // e is a multiple of 4 here, so the float4 stores are aligned
 #pragma unroll
-    for (int j = 0; j < BV; ++j) {
-      float* row = win_buf + ((size_t)p * win + lv + j) * ws + 2 * lu;
+        for (int p = 0; p < P; ++p)
 #pragma unroll
-      for (int i = 0; i < BU; ++i) {
-        const float2 q = acc[p][j][i];
-        if (q.x != 0.f) atomicAdd(row + 2 * i, q.x);
-        if (q.y != 0.f) atomicAdd(row + 2 * i + 1, q.y);
-        acc[p][j][i] = make_float2(0.f, 0.f);
+          for (int j = 0; j < BV; ++j)
+#pragma unroll
+            for (int i = 0; i < BU; i += 2) {
+              const int e = ((p * BV + j) * BU + i) * 2;
+              *(float4*)(dst + e) = make_float4(acc[p][j][i].x, acc[p][j][i].y, acc[p][j][i + 1].x, acc[p][j][i + 1].y);
+            }
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+          for (int j = 0; j < BV; ++j)
+#pragma unroll
+            for (int i = 0; i < BU; ++i) *(float2*)(dst + ((p * BV + j) * BU + i) * 2) = acc[p][j][i];
+      }
+      w.keys[rank] = key;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int j = 0; j < BV; ++j)
+#pragma unroll
+          for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
+    }
+    __syncwarp(w.wmask);
+    // the last warp of a CTA whose size is not a multiple of 32 has fewer
+    // lanes (wmask holds the low ones), so the stride is the lane count
+    const int nl = __popc(w.wmask);
+    for (int idx = lane; idx < cnt * F; idx += nl) {
+      const int s = idx / F;
+      const int e = idx - s * F;
+      const float v = w.slots[idx];
+      if (v != 0.f) {
+        const unsigned k2 = w.keys[s];
+        const int c = e & 1, q = e >> 1;
+        const int i = q % BU, j = (q / BU) % BV, p = q / (BU * BV);
+        const int lu = (int)(k2 & 0xFFFFu) * BU - w.wu0 + i;
+        const int lv = (int)(k2 >> 16) * BV - w.wv0 + j;
+        atomicAdd(w.buf + p * w.ps + lv * w.ws + 2 * lu + c, v);
       }
     }
+    __syncwarp(w.wmask);
+    m &= ~take;
   }
-}
-
-template <int BU, int BV, int P>
-__device__ __forceinline__ void flush_any(float2 (&acc)[P][BV][BU], unsigned key, float2* grid, int G, float* win_buf, int win,
-                                          int wu0, int wv0) {
-  if (key == kInvalid) return;
-  if (win > 0) {
-    const int lu = (int)(key & 0xFFFFu) * BU - wu0;
-    const int lv = (int)(key >> 16) * BV - wv0;
-    if (lu >= 0 && lv >= 0 && lu + BU <= win && lv + BV <= win) {
-      flush_window<BU, BV, P>(acc, lu, lv, win_buf, win);
-      return;
-    }
-  }
-  flush_global<BU, BV, P>(acc, key, grid, G);
-}
-
-template <int BU, int BV>
-__host__ __device__ constexpr int tab_floats_align() { return 4; }
-
-// Shared-memory layout helpers (bytes, 16-aligned).
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-template <int BU, int BV, int P>
-__host__ __device__ inline size_t grid_smem_tables(const Geometry& g) {
-  return align16((size_t)g.O * BU * g.nbu * 4) + align16((size_t)g.O * BV * g.nbv * 4);
-}
-
-template <int BU, int BV, int P>
-__host__ __device__ inline size_t grid_smem_records(const Geometry& g) {
-  // two buffers x teams x kRB x (meta + P values)
-  return 2 * (size_t)g.tpc * kRB * (16 + 8 * P);
 }
 
 // ---------------------------------------------------------------------------
-// The team's per-visibility step (shared by both schedules).
-template <int BU, int BV, int P>
-__device__ __forceinline__ void grid_step(const int4 m, const float2* __restrict__ vals, int au, int av, const Geometry& g,
-                                          const float* __restrict__ tabU, const float* __restrict__ tabV,
-                                          float2 (&acc)[P][BV][BU], unsigned& cur, float2* grid, float* win_buf, int win,
-                                          int wu0, int wv0) {
-  if (m.x == (int)kInvalid) return;
-  const int qu = m.x & 0xFFFF, qv = (int)((unsigned)m.x >> 16);
-  const int rqu = m.y & 0xFFFF, rqv = (int)((unsigned)m.y >> 16);
-  int tu = au - rqu;
-  tu += (tu < 0) ? g.nu : 0;
-  int tv = av - rqv;
-  tv += (tv < 0) ? g.nv : 0;
-  const unsigned key = (unsigned)(qu + tu) | ((unsigned)(qv + tv) << 16);
-  if (key != cur) {
-    flush_any<BU, BV, P>(acc, cur, grid, g.G, win_buf, win, wu0, wv0);
-    cur = key;
-  }
-  float wu[BU], wv[BV];
-  load_taps<BU>(tabU + m.z + tu * BU, wu);
-  load_taps<BV>(tabV + m.w + tv * BV, wv);
-  float2 V[P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) V[p] = vals[p];
-#pragma unroll
-  for (int j = 0; j < BV; ++j) {
-#pragma unroll
-    for (int i = 0; i < BU; ++i) {
-      const float w = wu[i] * wv[j];
-      const float2 w2 = make_float2(w, w);
-#pragma unroll
-      for (int p = 0; p < P; ++p) acc[p][j][i] = __ffma2_rn(w2, V[p], acc[p][j][i]);
-    }
-  }
-}
-
-// Stage batch b of a team's chunk into shared memory: each team thread loads
-// records l, l+ts, ... of the batch (Sec. 4: "each work-item loads one
-// visibility").
+// Staging: batch b of a team's chunk goes into shared memory. Each team
+// thread loads records l, l+ts, ... of the batch (Sec. 4: "each work-item
+// loads one visibility").
 template <int BU, int BV, int P>
 __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long long vend, int b, int l, int4* meta,
                                             float2* vals) {
@@ -368,33 +430,83 @@ __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Gridding kernel. The chunked schedule (win == 0) gives one chunk per team
-// with flushes to global memory (Sec. 4). The patch schedule (win > 0) uses
-// persistent CTAs that take work items (one patch plus a range of its
-// chunks), accumulate the patch window in shared memory and add it to the
-// grid at the end of each item.
+__device__ __forceinline__ unsigned box_key(const int4 m, int au, int av, const Geometry& g, int& tu, int& tv) {
+  const int qu = m.x & 0xFFFF, qv = (int)((unsigned)m.x >> 16);
+  const int rqu = m.y & 0xFFFF, rqv = (int)((unsigned)m.y >> 16);
+  tu = au - rqu;
+  tu += (tu < 0) ? g.nu : 0;
+  tv = av - rqv;
+  tv += (tv < 0) ? g.nv : 0;
+  return (unsigned)(qu + tu) | ((unsigned)(qv + tv) << 16);
+}
+
+// The convolution of one visibility into the thread's block (Sec. 3): Bu + Bv
+// taps from the padded tables, Bu*Bv tap products, Bu*Bv*P packed FMAs.
 template <int BU, int BV, int P>
+__device__ __forceinline__ void accumulate(const int4 m, int tu, int tv, const float2* __restrict__ vals,
+                                           const float* __restrict__ tabU, const float* __restrict__ tabV,
+                                           float2 (&acc)[P][BV][BU]) {
+  float wu[BU], wv[BV];
+  load_taps<BU>(tabU + m.z + tu * BU, wu);
+  load_taps<BV>(tabV + m.w + tv * BV, wv);
+  float2 V[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) V[p] = vals[p];
+#pragma unroll
+  for (int j = 0; j < BV; ++j) {
+#pragma unroll
+    for (int i = 0; i < BU; ++i) {
+      const float wgt = wu[i] * wv[j];
+      const float2 w2 = make_float2(wgt, wgt);
+#pragma unroll
+      for (int p = 0; p < P; ++p) acc[p][j][i] = __ffma2_rn(w2, V[p], acc[p][j][i]);
+    }
+  }
+}
+
+__device__ __forceinline__ void group_sync(const Args& a, unsigned wmask) {
+  if (a.warp_sync) __syncwarp(wmask);
+  else __syncthreads();
+}
+
+__device__ __forceinline__ unsigned warp_lane_mask() {
+  const int base = threadIdx.x & ~31;
+  const int n = (int)blockDim.x - base;
+  return n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Gridding kernel.
+//  - Chunked schedule (win == 0): one chunk per team, flushes to global
+//    memory with vector atomics (Sec. 4).
+//  - Patch schedule (win > 0): persistent CTAs take work items (a patch plus
+//    a range of its chunks). A CTA accumulates the patch window in shared
+//    memory through cooperative warp flushes, then adds the touched part of
+//    the window to the grid and leaves it zeroed for the next item.
+// Teams whose size divides 32 sit inside one warp and synchronise per warp
+// (warp_sync). Otherwise all teams of the CTA step through batches together.
+template <int BU, int BV, int P, bool PATCH>
 __global__ void grid_kernel(Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geometry& g = a.g;
-  float* tabU = (float*)smem;
-  float* tabV = (float*)(smem + align16((size_t)g.O * BU * g.nbu * 4));
-  unsigned char* rec = smem + grid_smem_tables<BU, BV, P>(g);
-  int4* meta0 = (int4*)rec;
-  int4* meta1 = meta0 + g.tpc * kRB;
-  float2* vals0 = (float2*)(meta1 + g.tpc * kRB);
-  float2* vals1 = vals0 + (size_t)g.tpc * kRB * P;
-  float* win_buf = (float*)(vals1 + (size_t)g.tpc * kRB * P);
+  const SmemLayout L = grid_layout<BU, BV, P>(g, blockDim.x, a.win);
+  float* tabU = (float*)(smem + L.tabU);
+  float* tabV = (float*)(smem + L.tabV);
+  int4* meta = (int4*)(smem + L.meta);
+  float2* vals = (float2*)(smem + L.vals);
 
   build_table<BU>(tabU, a, g.nbu);
   build_table<BV>(tabV, a, g.nbv);
 
   const int team = threadIdx.x / g.ts;
   const int l = threadIdx.x - team * g.ts;
-  const bool active = team < g.tpc;
   const int au = l % g.nu, av = l / g.nu;
   const int nb = (a.chunk_len + kRB - 1) / kRB;
+  const unsigned wmask = warp_lane_mask();
+  int4* const mt0 = meta + team * kRB;
+  int4* const mt1 = meta + (g.tpc + team) * kRB;
+  float2* const vl0 = vals + (size_t)team * kRB * P;
+  float2* const vl1 = vals + (size_t)(g.tpc + team) * kRB * P;
 
   float2 acc[P][BV][BU];
 #pragma unroll
@@ -404,93 +516,126 @@ __global__ void grid_kernel(Args a) {
 #pragma unroll
       for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
 
-  if (a.win == 0) {
+  if constexpr (!PATCH) {
     // ---- chunked schedule: one chunk per team
     const long long chunk = (long long)blockIdx.x * g.tpc + team;
     const long long vbeg = chunk * a.chunk_len;
-    const long long vend = (active && chunk < a.n_chunks) ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
-    int4* mt = meta0 + team * kRB;
-    float2* vl = vals0 + (size_t)team * kRB * P;
+    const long long vend = chunk < a.n_chunks ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
     __syncthreads();  // tables ready
     unsigned cur = kInvalid;
     for (int b = 0; b < nb; ++b) {
-      int4* mtb = (b & 1) ? mt + g.tpc * kRB : mt;
-      float2* vlb = (b & 1) ? vl + (size_t)g.tpc * kRB * P : vl;
-      if (active) stage_batch<BU, BV, P>(a, vbeg, vend, b, l, mtb, vlb);
-      __syncthreads();
-      if (active) {
+      int4* const mtb = (b & 1) ? mt1 : mt0;
+      float2* const vlb = (b & 1) ? vl1 : vl0;
+      stage_batch<BU, BV, P>(a, vbeg, vend, b, l, mtb, vlb);
+      group_sync(a, wmask);
 #pragma unroll 1
-        for (int r = 0; r < kRB; ++r) {
-          const int4 m = mtb[r];
-          grid_step<BU, BV, P>(m, vlb + r * P, au, av, g, tabU, tabV, acc, cur, a.grid, nullptr, 0, 0, 0);
+      for (int r = 0; r < kRB; ++r) {
+        const int4 m = mtb[r];
+        if (m.x == (int)kInvalid) continue;
+        int tu, tv;
+        const unsigned key = box_key(m, au, av, g, tu, tv);
+        if (key != cur) {
+          if (cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+          cur = key;
         }
+        accumulate<BU, BV, P>(m, tu, tv, vlb + r * P, tabU, tabV, acc);
       }
     }
-    if (active) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
-    return;
-  }
-
+    if (cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+  } else {
   // ---- patch schedule
   __shared__ int s_item;
-  const int win = a.win;
-  const int ws = win_stride(win);
-  const int win_floats = P * win * ws;
+  __shared__ int s_dirty[4];
+  WindowCtx w;
+  w.buf = (float*)(smem + L.win);
+  w.win = a.win;
+  w.ws = win_row_stride(a.win);
+  w.ps = win_plane_stride(a.win);
+  w.slots = (float*)(smem + L.slots) + (threadIdx.x >> 5) * kSlots * (2 * P * BU * BV);
+  w.keys = (unsigned*)(smem + L.keys) + (threadIdx.x >> 5) * kSlots;
+  w.wmask = wmask;
+  const int plane_floats = P * w.ps;
+  for (int i = threadIdx.x; i < plane_floats; i += blockDim.x) w.buf[i] = 0.f;
   const int n_work = *a.n_work;
+  int batch = 0;  // running batch counter: selects the staging buffer
   for (;;) {
-    __syncthreads();  // previous item fully flushed; tables ready on the first pass
-    if (threadIdx.x == 0) s_item = atomicAdd(a.work_next, 1);
-    for (int i = threadIdx.x; i < win_floats; i += blockDim.x) win_buf[i] = 0.f;
+    __syncthreads();  // previous item flushed, window zero, tables ready
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(a.work_next, 1);
+      s_dirty[0] = a.win; s_dirty[1] = a.win; s_dirty[2] = 0; s_dirty[3] = 0;
+    }
     __syncthreads();
     const int item = s_item;
     if (item >= n_work) break;
     const int4 wk = a.work[item];
-    const int wu0 = wk.x, wv0 = wk.y;
-    // teams take the item's chunks round-robin, all in lockstep batches
+    w.wu0 = wk.x;
+    w.wv0 = wk.y;
+    int4 dirty = make_int4(a.win, a.win, 0, 0);
     const int n_item_chunks = wk.w - wk.z;
     const int rounds = (n_item_chunks + g.tpc - 1) / g.tpc;
-    int4* mt = meta0 + team * kRB;
-    float2* vl = vals0 + (size_t)team * kRB * P;
     for (int rd = 0; rd < rounds; ++rd) {
       const int ci = rd * g.tpc + team;
       long long vbeg = 0, vend = 0;
-      if (active && ci < n_item_chunks) {
+      if (ci < n_item_chunks) {
         const long long chunk = a.chunk_order[wk.z + ci];
         vbeg = chunk * a.chunk_len;
         vend = min(vbeg + a.chunk_len, a.n_vis);
       }
       unsigned cur = kInvalid;
-      for (int b = 0; b < nb; ++b) {
-        int4* mtb = (b & 1) ? mt + g.tpc * kRB : mt;
-        float2* vlb = (b & 1) ? vl + (size_t)g.tpc * kRB * P : vl;
-        if (active) stage_batch<BU, BV, P>(a, vbeg, vend, b, l, mtb, vlb);
-        __syncthreads();
-        if (active) {
+      for (int b = 0; b < nb; ++b, ++batch) {
+        int4* const mtb = (batch & 1) ? mt1 : mt0;
+        float2* const vlb = (batch & 1) ? vl1 : vl0;
+        stage_batch<BU, BV, P>(a, vbeg, vend, b, l, mtb, vlb);
+        group_sync(a, wmask);
 #pragma unroll 1
-          for (int r = 0; r < kRB; ++r) {
-            const int4 m = mtb[r];
-            grid_step<BU, BV, P>(m, vlb + r * P, au, av, g, tabU, tabV, acc, cur, a.grid, win_buf, win, wu0, wv0);
+        for (int r = 0; r < kRB; ++r) {
+          const int4 m = mtb[r];
+          const bool valid = m.x != (int)kInvalid;
+          int tu = 0, tv = 0;
+          unsigned key = cur;
+          if (valid) key = box_key(m, au, av, g, tu, tv);
+          window_flush<BU, BV, P>(valid && key != cur && cur != kInvalid, cur, acc, a.grid, g.G, w, dirty);
+          if (valid) {
+            cur = key;
+            accumulate<BU, BV, P>(m, tu, tv, vlb + r * P, tabU, tabV, acc);
           }
         }
       }
-      if (active) flush_any<BU, BV, P>(acc, cur, a.grid, g.G, win_buf, win, wu0, wv0);
+      window_flush<BU, BV, P>(cur != kInvalid, cur, acc, a.grid, g.G, w, dirty);
+    }
+    if (dirty.z > dirty.x) {
+      atomicMin(&s_dirty[0], dirty.x);
+      atomicMin(&s_dirty[1], dirty.y);
+      atomicMax(&s_dirty[2], dirty.z);
+      atomicMax(&s_dirty[3], dirty.w);
     }
     __syncthreads();
-    // add the window to the grid: coalesced float4 atomics, all-zero vectors skipped
-    const int rowf4 = win / 2;  // float4 (two cells) per window row (win even)
-    const int total = P * win * rowf4;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int c4 = i % rowf4;
-      const int rowi = i / rowf4;
-      const int vv = rowi % win;
-      const int p = rowi / win;
-      const int gu = wu0 + 2 * c4, gv = wv0 + vv;
-      const float* src = win_buf + (size_t)rowi * ws + 4 * c4;
-      const float4 q = make_float4(src[0], src[1], src[2], src[3]);
-      const bool nz = (q.x != 0.f) | (q.y != 0.f) | (q.z != 0.f) | (q.w != 0.f);
-      if (nz && gu >= 0 && gv >= 0 && gu + 1 < g.G && gv < g.G)
-        atomicAdd((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
+    // add the touched rectangle of the window to the grid (float4 = two cells,
+    // coalesced vector atomics, all-zero vectors skipped) and zero it again
+    const int u_lo = s_dirty[0] & ~1, u_hi = (s_dirty[2] + 1) & ~1;
+    const int v_lo = s_dirty[1], v_hi = s_dirty[3];
+    if (u_hi > u_lo && v_hi > v_lo) {
+      const int cols = (u_hi - u_lo) >> 1, rows = v_hi - v_lo;
+      const int total = P * rows * cols;
+      for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int c = i % cols;
+        const int rr = i / cols;
+        const int vv = v_lo + rr % rows;
+        const int p = rr / rows;
+        const int lu = u_lo + 2 * c;
+        float4* src = (float4*)(w.buf + p * w.ps + vv * w.ws + 2 * lu);
+        const float4 q = *src;
+        const bool nz = (q.x != 0.f) | (q.y != 0.f) | (q.z != 0.f) | (q.w != 0.f);
+        if (nz) {
+          const int gu = w.wu0 + lu, gv = w.wv0 + vv;
+          if (gu >= 0 && gv >= 0 && gu + 1 < g.G && gv < g.G)
+            atomicAdd((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
+          *src = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
     }
   }
+  }  // PATCH
 }
 
 // ---------------------------------------------------------------------------
@@ -498,7 +643,7 @@ __global__ void grid_kernel(Args a) {
 // block in registers and reloads them only when the box moves (the read-side
 // analogue of a flush). Per visibility it forms P complex partial sums over
 // its block. The team reduces them through shared memory: each thread stores
-// its partials, then each thread sums one column of (record, component)
+// its partials, then each thread sums whole columns of (record, component)
 // outputs.
 template <int BU, int BV, int P>
 __device__ __forceinline__ void load_block(float2 (&gb)[P][BV][BU], unsigned key, const float2* __restrict__ grid, int G) {
@@ -531,19 +676,13 @@ __device__ __forceinline__ void load_block(float2 (&gb)[P][BV][BU], unsigned key
 }
 
 template <int BU, int BV, int P>
-__host__ __device__ inline size_t degrid_smem_bytes(const Geometry& g) {
-  const int tsp = g.ts | 1;
-  return grid_smem_tables<BU, BV, P>(g) + (size_t)g.tpc * kRBD * 16 + align16((size_t)g.tpc * kRBD * 2 * P * tsp * 4);
-}
-
-template <int BU, int BV, int P>
 __global__ void degrid_kernel(Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geometry& g = a.g;
-  float* tabU = (float*)smem;
-  float* tabV = (float*)(smem + align16((size_t)g.O * BU * g.nbu * 4));
-  int4* meta_all = (int4*)(smem + grid_smem_tables<BU, BV, P>(g));
-  float* red_all = (float*)(meta_all + g.tpc * kRBD);
+  const SmemLayout L = degrid_layout<BU, BV, P>(g, blockDim.x, 0);
+  float* tabU = (float*)(smem + L.tabU);
+  float* tabV = (float*)(smem + L.tabV);
+  int4* meta = (int4*)(smem + L.meta);
   const int tsp = g.ts | 1;
 
   build_table<BU>(tabU, a, g.nbu);
@@ -551,93 +690,247 @@ __global__ void degrid_kernel(Args a) {
 
   const int team = threadIdx.x / g.ts;
   const int l = threadIdx.x - team * g.ts;
-  const bool active = team < g.tpc;
   const int au = l % g.nu, av = l / g.nu;
+  const unsigned wmask = warp_lane_mask();
   const long long chunk = (long long)blockIdx.x * g.tpc + team;
   const long long vbeg = chunk * a.chunk_len;
-  const long long vend = (active && chunk < a.n_chunks) ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
-  int4* mt = meta_all + team * kRBD;
-  float* red = red_all + (size_t)team * kRBD * 2 * P * tsp;
+  const long long vend = chunk < a.n_chunks ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
+  int4* const mt0 = meta + team * kRBD;
+  int4* const mt1 = meta + (g.tpc + team) * kRBD;
+  float* red = (float*)(smem + L.red) + (size_t)team * kRBD * 2 * P * tsp;
   const int nb = (a.chunk_len + kRBD - 1) / kRBD;
 
   float2 gb[P][BV][BU];
   unsigned cur = kInvalid;
   __syncthreads();
   for (int b = 0; b < nb; ++b) {
-    if (active) {
-      for (int r = l; r < kRBD; r += g.ts) {
-        const long long k = vbeg + (long long)b * kRBD + r;
-        int4 m;
-        m.x = (int)kInvalid;
-        if (k < vend && !make_meta<BU, BV>(a, a.uv[k], m)) atomicAdd(a.skipped, 1ULL);
-        mt[r] = m;
-      }
+    int4* const mtb = (b & 1) ? mt1 : mt0;
+    for (int r = l; r < kRBD; r += g.ts) {
+      const long long k = vbeg + (long long)b * kRBD + r;
+      int4 m;
+      m.x = (int)kInvalid;
+      if (k < vend && !make_meta<BU, BV>(a, a.uv[k], m)) atomicAdd(a.skipped, 1ULL);
+      mtb[r] = m;
     }
-    __syncthreads();
-    if (active) {
+    group_sync(a, wmask);
 #pragma unroll 1
-      for (int r = 0; r < kRBD; ++r) {
-        const int4 m = mt[r];
-        float2 s[P];
+    for (int r = 0; r < kRBD; ++r) {
+      const int4 m = mtb[r];
+      float2 s[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) s[p] = make_float2(0.f, 0.f);
-        if (m.x != (int)kInvalid) {
-          const int qu = m.x & 0xFFFF, qv = (int)((unsigned)m.x >> 16);
-          const int rqu = m.y & 0xFFFF, rqv = (int)((unsigned)m.y >> 16);
-          int tu = au - rqu;
-          tu += (tu < 0) ? g.nu : 0;
-          int tv = av - rqv;
-          tv += (tv < 0) ? g.nv : 0;
-          const unsigned key = (unsigned)(qu + tu) | ((unsigned)(qv + tv) << 16);
-          if (key != cur) {
-            load_block<BU, BV, P>(gb, key, a.grid, g.G);
-            cur = key;
-          }
-          float wu[BU], wv[BV];
-          load_taps<BU>(tabU + m.z + tu * BU, wu);
-          load_taps<BV>(tabV + m.w + tv * BV, wv);
+      for (int p = 0; p < P; ++p) s[p] = make_float2(0.f, 0.f);
+      if (m.x != (int)kInvalid) {
+        int tu, tv;
+        const unsigned key = box_key(m, au, av, g, tu, tv);
+        if (key != cur) {
+          load_block<BU, BV, P>(gb, key, a.grid, g.G);
+          cur = key;
+        }
+        float wu[BU], wv[BV];
+        load_taps<BU>(tabU + m.z + tu * BU, wu);
+        load_taps<BV>(tabV + m.w + tv * BV, wv);
 #pragma unroll
-          for (int j = 0; j < BV; ++j) {
+        for (int j = 0; j < BV; ++j) {
 #pragma unroll
-            for (int i = 0; i < BU; ++i) {
-              const float w = wu[i] * wv[j];
-              const float2 w2 = make_float2(w, w);
+          for (int i = 0; i < BU; ++i) {
+            const float wgt = wu[i] * wv[j];
+            const float2 w2 = make_float2(wgt, wgt);
 #pragma unroll
-              for (int p = 0; p < P; ++p) s[p] = __ffma2_rn(w2, gb[p][j][i], s[p]);
-            }
+            for (int p = 0; p < P; ++p) s[p] = __ffma2_rn(w2, gb[p][j][i], s[p]);
           }
         }
+      }
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-          red[(r * 2 * P + 2 * p) * tsp + l] = s[p].x;
-          red[(r * 2 * P + 2 * p + 1) * tsp + l] = s[p].y;
-        }
+      for (int p = 0; p < P; ++p) {
+        red[(r * 2 * P + 2 * p) * tsp + l] = s[p].x;
+        red[(r * 2 * P + 2 * p + 1) * tsp + l] = s[p].y;
       }
     }
-    __syncthreads();
-    if (active) {
-      // each team thread sums whole columns: output o = (record, component)
-      for (int o = l; o < kRBD * 2 * P; o += g.ts) {
-        const int r = o / (2 * P);
-        const long long k = vbeg + (long long)b * kRBD + r;
-        if (k < vend) {
-          const float* col = red + (size_t)o * tsp;
-          float sum = 0.f;
-          for (int t = 0; t < g.ts; ++t) sum += col[t];
-          if (a.weights) sum *= a.weights[k];
-          ((float*)a.vis_out)[k * 2 * P + (o - r * 2 * P)] = sum;
-        }
+    group_sync(a, wmask);
+    // each team thread sums whole columns: output o = (record, component)
+    for (int o = l; o < kRBD * 2 * P; o += g.ts) {
+      const int r = o / (2 * P);
+      const long long k = vbeg + (long long)b * kRBD + r;
+      if (k < vend) {
+        const float* col = red + (size_t)o * tsp;
+        float sum = 0.f;
+        for (int t = 0; t < g.ts; ++t) sum += col[t];
+        if (a.weights) sum *= a.weights[k];
+        ((float*)a.vis_out)[k * 2 * P + (o - r * 2 * P)] = sum;
       }
     }
-    __syncthreads();
+    // the next batch stages into the other meta buffer; its group_sync
+    // separates these reads of `red` from the next writes
   }
 }
 
-// Function table entry for one (Bu, Bv, P) instantiation.
+// Function table entry for one (Bu, Bv, P) instantiation, with its
+// shared-memory layout functions.
 struct KernelEntry {
   int bu, bv, p;
-  const void* grid_fn;
+  const void* grid_fn;        // chunked schedule
+  const void* grid_patch_fn;  // patch schedule
   const void* degrid_fn;
+  size_t (*grid_smem)(const Geometry&, int nthreads, int win);
+  size_t (*degrid_smem)(const Geometry&, int nthreads, int win);
+};
+
+template <int BU, int BV, int P>
+size_t grid_smem_bytes(const Geometry& g, int nthreads, int win) {
+  return grid_layout<BU, BV, P>(g, nthreads, win).total;
+}
+
+template <int BU, int BV, int P>
+size_t degrid_smem_bytes(const Geometry& g, int nthreads, int win) {
+  return degrid_layout<BU, BV, P>(g, nthreads, win).total;
+}
+
+}  // namespace gbg
+
+namespace gbg {
+
+// ---------------------------------------------------------------------------
+// Batched gridding: many independent grids (channels x w-planes, Sec. 5 grids
+// each w-slice with its own kernel instance) in ONE persistent launch. Every
+// item has its own visibilities, GCF support S, kernel table and grid; G, O,
+// P, the block shape and the storage format are common. Work units are runs of
+// chunks of one item, sorted by cost on the host; persistent CTAs take them
+// from an atomic counter, rebuild their padded tables when the item changes,
+// and grid with the chunked schedule (flushes to global memory).
+struct BatchItem {
+  const double2* uv;
+  const void* vis;
+  const float* weights;
+  const void* table;
+  float2* grid;
+  long long n_vis;
+  int S;
+  int pad;
+};
+
+struct BatchArgs {
+  int G, O, log2O, P;
+  int fmt;
+  int chunk_len;
+  int nb_max;           // table capacity: largest bin width over the items
+  int tpc_max;          // record-buffer capacity in teams
+  const BatchItem* items;
+  const int4* units;    // {item, first chunk, chunks, 0}
+  int n_units;
+  int* unit_next;
+  unsigned long long* skipped;
+};
+
+template <int BU, int BV, int P>
+__host__ __device__ inline SmemLayout batch_layout(int O, int nb_max, int tpc_max) {
+  SmemLayout L{};
+  size_t off = 0;
+  L.tabU = off; off += align16((size_t)O * BU * nb_max * 4);
+  L.tabV = off; off += align16((size_t)O * BV * nb_max * 4);
+  L.meta = off; off += align16((size_t)2 * tpc_max * kRB * 16);
+  L.vals = off; off += align16((size_t)2 * tpc_max * kRB * P * 8);
+  L.total = off;
+  return L;
+}
+
+template <int BU, int BV, int P>
+__global__ void grid_batch_kernel(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout L = batch_layout<BU, BV, P>(b.O, b.nb_max, b.tpc_max);
+  float* tabU = (float*)(smem + L.tabU);
+  float* tabV = (float*)(smem + L.tabV);
+  int4* meta = (int4*)(smem + L.meta);
+  float2* vals = (float2*)(smem + L.vals);
+  __shared__ int s_unit;
+  int loaded = -1;  // item whose tables are in shared memory (uniform across the CTA)
+  const int nbat = (b.chunk_len + kRB - 1) / kRB;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_unit = atomicAdd(b.unit_next, 1);
+    __syncthreads();
+    const int unit = s_unit;
+    if (unit >= b.n_units) break;
+    const int4 u = b.units[unit];
+    const BatchItem it = b.items[u.x];
+    Args a;
+    a.g.G = b.G; a.g.S = it.S; a.g.O = b.O; a.g.log2O = b.log2O; a.g.h = (it.S - 1) / 2; a.g.P = P;
+    a.g.nbu = ((it.S + BU - 1 + BU - 1) / BU) * BU;
+    a.g.nbv = ((it.S + BV - 1 + BV - 1) / BV) * BV;
+    a.g.nu = a.g.nbu / BU;
+    a.g.nv = a.g.nbv / BV;
+    a.g.ts = a.g.nu * a.g.nv;
+    a.g.tpc = min(b.tpc_max, (int)blockDim.x / a.g.ts);
+    a.n_vis = it.n_vis;
+    a.uv = it.uv;
+    a.vis = it.vis;
+    a.vis_fmt = b.fmt;
+    a.weights = it.weights;
+    a.table = it.table;
+    a.tab_fmt = b.fmt;
+    a.grid = it.grid;
+    a.chunk_len = b.chunk_len;
+    a.n_chunks = (it.n_vis + b.chunk_len - 1) / b.chunk_len;
+    a.warp_sync = 0;
+    a.skipped = b.skipped;
+    const Geometry& g = a.g;
+    if (u.x != loaded) {
+      build_table<BU>(tabU, a, g.nbu);
+      build_table<BV>(tabV, a, g.nbv);
+      loaded = u.x;
+      __syncthreads();
+    }
+    const int team = threadIdx.x / g.ts;
+    const int l = threadIdx.x - team * g.ts;
+    const bool active = team < u.z;  // u.z <= tpc chunks in this unit
+    const int au = l % g.nu, av = l / g.nu;
+    const long long chunk = (long long)u.y + team;
+    const long long vbeg = chunk * b.chunk_len;
+    const long long vend = active ? min(vbeg + b.chunk_len, it.n_vis) : vbeg;
+    int4* const mt0 = meta + team * kRB;
+    int4* const mt1 = meta + (b.tpc_max + team) * kRB;
+    float2* const vl0 = vals + (size_t)team * kRB * P;
+    float2* const vl1 = vals + (size_t)(b.tpc_max + team) * kRB * P;
+    float2 acc[P][BV][BU];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 0; j < BV; ++j)
+#pragma unroll
+        for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
+    unsigned cur = kInvalid;
+    for (int bt = 0; bt < nbat; ++bt) {
+      int4* const mtb = (bt & 1) ? mt1 : mt0;
+      float2* const vlb = (bt & 1) ? vl1 : vl0;
+      if (team < g.tpc) stage_batch<BU, BV, P>(a, vbeg, vend, bt, l, mtb, vlb);
+      __syncthreads();
+      if (active) {
+#pragma unroll 1
+        for (int r = 0; r < kRB; ++r) {
+          const int4 m = mtb[r];
+          if (m.x == (int)kInvalid) continue;
+          int tu, tv;
+          const unsigned key = box_key(m, au, av, g, tu, tv);
+          if (key != cur) {
+            if (cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+            cur = key;
+          }
+          accumulate<BU, BV, P>(m, tu, tv, vlb + r * P, tabU, tabV, acc);
+        }
+      }
+    }
+    if (active && cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+  }
+}
+
+template <int BU, int BV, int P>
+size_t batch_smem_bytes(int O, int nb_max, int tpc_max) {
+  return batch_layout<BU, BV, P>(O, nb_max, tpc_max).total;
+}
+
+struct BatchKernelEntry {
+  int bu, bv, p;
+  const void* fn;
+  size_t (*smem)(int O, int nb_max, int tpc_max);
 };
 
 }  // namespace gbg

@@ -32,6 +32,11 @@ def gb():
     return gb
 
 
+def kb32(w):
+    """The oracle's KB table rounded to FP32 on the host, as float64 (the same input for both sides)."""
+    return oracle.kb_table(w.S, w.oversample, w.beta).astype(np.float32).astype(np.float64)
+
+
 def rel_l2(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
@@ -42,8 +47,8 @@ def test_grid_backward_is_weighted_adjoint(gb, schedule):
     w = synth.scaled_down(synth.quad_pol(), 60_000)
     rng = np.random.default_rng(1)
     wt = rng.uniform(0.2, 2.0, w.n_vis).astype(np.float32)
-    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta)
-    t64 = table.cpu().numpy().astype(np.float64)
+    t64 = kb32(w)
+    table = torch.from_numpy(t64.astype(np.float32)).cuda()
     plan = gb.Plan(w.G, w.S, w.oversample, 4, B=2, schedule=schedule)
     uv = torch.from_numpy(w.uv).cuda()
     vis = torch.from_numpy(w.vis).cuda().requires_grad_(True)
@@ -61,8 +66,8 @@ def test_grid_backward_is_weighted_adjoint(gb, schedule):
 def test_degrid_backward_is_grid(gb):
     from paper_1605_07023_gb300.autograd import degrid_op
     w = synth.scaled_down(synth.quad_pol(), 40_000)
-    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta)
-    t64 = table.cpu().numpy().astype(np.float64)
+    t64 = kb32(w)
+    table = torch.from_numpy(t64.astype(np.float32)).cuda()
     plan = gb.Plan(w.G, w.S, w.oversample, 4, B=2)
     rng = np.random.default_rng(2)
     g0 = (rng.standard_normal((4, w.G, w.G)) + 1j * rng.standard_normal((4, w.G, w.G))).astype(np.complex64)
@@ -81,14 +86,16 @@ def test_differentiation_workload_finite_differences(gb):
     w = synth.differentiation()
     assert w.n_vis == 1_000_000
     target = torch.from_numpy(synth.gaussian_sources_image(w.G, 5, seed=0)).cuda()
-    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta)
+    table = torch.from_numpy(kb32(w).astype(np.float32)).cuda()
     plan = gb.Plan(w.G, w.S, w.oversample, 1, B=2)
     uv = torch.from_numpy(w.uv).cuda()
     wt = torch.from_numpy(w.weights).cuda()
 
-    def loss_of_grid(g):  # FP64 loss from the FP32 grid: sum |FFT(grid) - target|^2
-        img = torch.fft.fftshift(torch.fft.ifft2(torch.fft.ifftshift(g.to(torch.complex128)[0]), norm="forward"))
-        return torch.sum(torch.abs(img - target) ** 2)
+    def image(g):  # FFT of the FP32 grid, in FP64
+        return torch.fft.fftshift(torch.fft.ifft2(torch.fft.ifftshift(g.to(torch.complex128)[0]), norm="forward"))
+
+    def loss_of_grid(g):  # loss = sum |FFT(grid) - target|^2
+        return torch.sum(torch.abs(image(g) - target) ** 2)
 
     vis = torch.from_numpy(w.vis).cuda().requires_grad_(True)
     g = grid_op(plan, uv, vis, wt, table)
@@ -104,16 +111,32 @@ def test_differentiation_workload_finite_differences(gb):
     for k in ks:
         one = torch.zeros((1, 1), dtype=torch.complex64, device="cuda")
         gk = torch.zeros_like(g0)
+        fd = {}
         for part, dv in (("re", 1.0 + 0j), ("im", 1j)):
             one.fill_(dv)
             gk.zero_()
             gb.grid(plan, uv[k:k + 1].contiguous(), one, wt[k:k + 1].contiguous(), table, gk)
-            lp = float(loss_of_grid(g0 + h * gk))
-            lm = float(loss_of_grid(g0 - h * gk))
-            fd = (lp - lm) / (2 * h)
-            an = grad[k].real if part == "re" else grad[k].imag
-            # PyTorch's complex gradient is dL/dRe + i dL/dIm
-            err = abs(fd - an) / max(abs(an), 1e-30)
-            worst = max(worst, err)
-            assert err <= 1e-3, (k, part, fd, an)
+            # central difference L(g0 + h gk) - L(g0 - h gk), differenced pixel by pixel before the
+            # sum: the loss is about 1e16 and the difference about 1e2, so subtracting the two sums
+            # would lose the difference to FP64 rounding
+            rp = torch.abs(image(g0 + h * gk) - target) ** 2
+            rm = torch.abs(image(g0 - h * gk) - target) ** 2
+            fd[part] = float(torch.sum(rp - rm)) / (2 * h)
+        # PyTorch's complex gradient is dL/dRe + i dL/dIm; compare as complex numbers, relative to
+        # the gradient's magnitude at this visibility (one component can be 1000x the other)
+        fdc = fd["re"] + 1j * fd["im"]
+        err = abs(fdc - grad[k]) / abs(grad[k])
+        worst = max(worst, err)
+        assert err <= 1e-3, (k, fdc, grad[k])
     assert worst <= 1e-3
+
+    # the whole gradient against an FP64 pipeline built from the oracle: oracle grid, FP64 FFT,
+    # oracle adjoint (degrid) of dL/dgrid
+    t64 = kb32(w)
+    g64, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, t64)
+    tgt = synth.gaussian_sources_image(w.G, 5, seed=0)
+    A = np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(g64[0]), norm="forward")) - tgt
+    dLdg = 2 * np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(A), norm="backward"))  # adjoint of the unnormalised inverse FFT
+    ref, _ = oracle.degrid(w.G, w.S, w.oversample, w.uv, dLdg[None], t64)
+    ref = ref[:, 0] * w.weights
+    assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) <= 1e-5

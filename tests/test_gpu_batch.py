@@ -1,0 +1,93 @@
+"""Batched gridding (many grids, uneven counts, per-grid S) in one persistent launch, and in a CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_07023_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1605_07023_gb300 as gb
+    return gb
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def small_batch(n_chan=3, total=600_000, seed=0):
+    """A reduced version of the batching workload: n_chan channels x 8 w-planes, G=1024, S by plane."""
+    return synth.batched(seed=seed, n_chan=n_chan, total=total)
+
+
+def device_items(ws):
+    items = []
+    for w in ws:
+        t64 = oracle.kb_table(w.S, w.oversample, w.beta).astype(np.float32)
+        items.append(dict(uv=torch.from_numpy(w.uv).cuda(), vis=torch.from_numpy(w.vis).cuda(),
+                          weights=torch.from_numpy(w.weights).cuda(), table=torch.from_numpy(t64).cuda(),
+                          grid=torch.zeros((1, w.G, w.G), dtype=torch.complex64, device="cuda"), S=w.S))
+    return items
+
+
+@pytest.mark.parametrize("B", [(2, 2), (1, 1), (3, 3), (4, 2)])
+def test_batch_matches_oracle(gb, B):
+    ws = [w for row in small_batch() for w in row]
+    items = device_items(ws)
+    bp = gb.BatchPlan(1024, 8, 1, Bu=B[0], Bv=B[1], max_S=15)
+    bp.set(items)
+    bp.execute()
+    torch.cuda.synchronize()
+    for w, it in zip(ws, items):
+        ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
+        assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, (w.name, B)
+    assert bp.skipped() == 0
+
+
+def test_batch_cuda_graph_replay(gb):
+    ws = [w for row in small_batch(n_chan=2, total=300_000, seed=1) for w in row]
+    items = device_items(ws)
+    bp = gb.BatchPlan(1024, 8, 1, Bu=2, Bv=2, max_S=15)
+    bp.set(items)
+    bp.execute()                    # warm up outside the capture
+    torch.cuda.synchronize()
+    for it in items:
+        it["grid"].zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bp.execute()
+    for it in items:
+        it["grid"].zero_()
+    graph.replay()
+    graph.replay()                  # gridding accumulates: two replays give twice the grid
+    torch.cuda.synchronize()
+    for w, it in zip(ws, items):
+        ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
+        assert rel_l2(it["grid"].cpu().numpy()[0], 2 * ref[0]) <= 1e-5
+
+
+def test_batch_empty_and_invalid(gb):
+    bp = gb.BatchPlan(64, 8, 1, Bu=2, Bv=2, max_S=7)
+    bp.set([])
+    bp.execute()
+    w = synth.random_uniform(64, 7, 8, 1, 1000, seed=2)
+    uv = w.uv.copy()
+    uv[:10, 0] = 500.0                  # off the grid: skipped
+    w.uv = uv
+    items = device_items([w, synth.Workload("empty", 64, 7, 8, 1, np.zeros((0, 2)), np.zeros((0, 1), np.complex64),
+                                            np.zeros(0, np.float32), beta=2.34 * 7)])
+    bp.set(items)
+    bp.execute()
+    torch.cuda.synchronize()
+    ref, sk = oracle.grid(64, 7, 8, w.uv, w.vis, w.weights, items[0]["table"].cpu().numpy().astype(np.float64))
+    assert sk == 10 and bp.skipped() == 10
+    assert rel_l2(items[0]["grid"].cpu().numpy()[0], ref[0]) <= 1e-5
+    with pytest.raises(gb.GridderError):
+        bad = dict(items[0], S=9)      # S above max_S
+        bp.set([bad])

@@ -145,6 +145,18 @@ def test_grid_random_positions_and_weights(gb, schedule, npol):
     check_grid(gb, w, 1, 1, schedule)
 
 
+@pytest.mark.parametrize("npol", [1, 4])
+@pytest.mark.parametrize("Bu,Bv", [(1, 1), (2, 1), (3, 3), (4, 4), (2, 2)])
+@pytest.mark.parametrize("threads", [0, 224, 1000])
+def test_patch_schedule_partial_warps(gb, npol, Bu, Bv, threads):
+    """Patch schedule for team sizes that leave a partial last warp (49, 28, 9 threads per team)."""
+    w = synth.random_uniform(256, 7, 8, npol, 30_011, seed=Bu * 10 + Bv + npol)
+    try:
+        check_grid(gb, w, Bu, Bv, "patch", threads=threads)
+    except gb.GridderError as e:      # a CTA size that cannot hold the window is refused, not run
+        assert e.code == -2
+
+
 @pytest.mark.parametrize("chunk", [1, 7, 16, 33, 1024])
 def test_grid_chunk_lengths(gb, chunk):
     w = synth.scaled_down(quad_pol(), 40_000)
