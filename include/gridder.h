@@ -205,6 +205,41 @@ int grid_batch_describe(grid_batch_t batch, int* threads, int* n_units, int* cta
 void grid_batch_destroy(grid_batch_t batch);
 const char* grid_batch_last_error(void);
 
+/*
+ * Gridding without device allocation. The paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc:
+ *  - a real-time pipeline that reserves all of its device memory at start-up
+ *    and may not allocate while observing;
+ *  - code that runs while a stream is being captured into a CUDA graph;
+ *  - a host framework that owns the device heap through its own allocator.
+ * Such callers cannot create a plan, because grid_plan_create and the patch
+ * schedule allocate scratch.
+ *
+ * grid_patch_static() takes the plan parameters directly and grids exactly
+ * as grid() does with GRID_SCHED_PATCH and 64-visibility chunks. The other
+ * arguments and the accumulate semantics are those of grid(). Its binning
+ * scratch lives in one file-scope device array of about 1.9 MB, which every
+ * GPU that loads the library holds until the process exits.
+ *  - Limits: at most 8,388,608 visibilities per call and at most 16,384 grid
+ *    patches (patches are 32 cells at npol 4, 48 at npol 2, 96 at npol 1).
+ *    A larger call returns GRID_ERR_INVALID with a message and queues
+ *    nothing.
+ *  - Allocation: it calls no cudaMalloc, no cudaFree and no allocating
+ *    library routine; it only enqueues memsets and kernels on `stream`.
+ *  - First call: the first call on each device looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current. Make that first
+ *    call before any stream capture.
+ *  - Concurrency: all calls share the one array. Calls whose work overlaps
+ *    on the GPU (other streams, other host threads) race and give wrong
+ *    results; serialise them.
+ * The message of the last error on the calling thread is in
+ * grid_patch_static_last_error().
+ */
+int grid_patch_static(int G, int S, int oversample, int npol, int Bu, int Bv, int precision, int64_t n_vis,
+                      const double* uv, const void* vis, const float* weights, const void* kernel_table, void* grid,
+                      cudaStream_t stream);
+const char* grid_patch_static_last_error(void);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* grid_last_error(void);
 

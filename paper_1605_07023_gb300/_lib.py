@@ -23,7 +23,8 @@ SCHED = {"chunked": 0, "patch": 1}
 EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
            "grid_last_error", "grid_device_info", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
-           "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error")
+           "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
+           "grid_patch_static", "grid_patch_static_last_error")
 
 
 class GridBatchItem(ctypes.Structure):
