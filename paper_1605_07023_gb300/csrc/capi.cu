@@ -59,7 +59,7 @@ const KernelEntry* find_kernel(int bu, int bv, int p) {
 }
 
 size_t tables_bytes(const Geometry& g, int bu, int bv) {
-  return a16((size_t)g.O * bu * g.nbu * 4) + a16((size_t)g.O * bv * g.nbv * 4);
+  return a16((size_t)g.O * bu * g.nbu * 8) + a16((size_t)g.O * bv * g.nbv * 8);
 }
 
 void free_patch(grid_plan_s* pl) {
@@ -225,7 +225,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     s.n_patches = s.n_pu * s.n_pu;
     s.halo_lo = halo;
     s.win = win;
-    s.max_chunks = 128;
+    s.max_chunks = 256;
   }
   pl->smem_grid = k->grid_smem(g, pl->threads, win);
   pl->smem_degrid = k->degrid_smem(g, pl->threads, 0);

@@ -100,6 +100,87 @@ __device__ __forceinline__ bool fine_cell(double x, int log2O, int halfG, int& C
   return true;
 }
 
+// L2 cache policies. The inputs (uv, visibilities, weights) are read once and
+// stream through L2 (evict first, no L1 allocation). The grid is updated or
+// read many times and should stay resident in L2 (evict last): it is about
+// the size of GB300's L2, and the streaming inputs would otherwise push it out.
+__device__ __forceinline__ unsigned long long policy_stream() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long policy_keep() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy_stream()));
+  return v;
+}
+// grid reads (degridding): keep the lines in L2
+__device__ __forceinline__ float4 ld_keep(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(policy_keep()));
+  return v;
+}
+__device__ __forceinline__ float2 ld_keep(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(policy_keep()));
+  return v;
+}
+// grid atomics: vector reductions that keep the grid's lines in L2
+__device__ __forceinline__ void red_keep(float4* p, float4 v) {
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(policy_keep())
+               : "memory");
+}
+__device__ __forceinline__ void red_keep(float2* p, float2 v) {
+  asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(policy_keep())
+               : "memory");
+}
+// output visibilities (degridding): written once
+__device__ __forceinline__ void st_stream(float* p, float v) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy_stream()) : "memory");
+}
+
 __device__ __forceinline__ float load_tap(const void* table, int fmt, int idx) {
   if (fmt == FMT_BF16) return __bfloat162float(((const __nv_bfloat16*)table)[idx]);
   if (fmt == FMT_F16) return __half2float(((const __half*)table)[idx]);
@@ -108,7 +189,7 @@ __device__ __forceinline__ float load_tap(const void* table, int fmt, int idx) {
 
 // Zero-padded, phase-expanded 1-D tables: tab[(r*B + rem)*nb + k] = T[r][k - rem]
 // for 0 <= k - rem < S, else 0. A thread at block position t reads taps
-// tab[(r*B + rem)*nb + t*B + i], i < B.
+// tab[(r*B + rem)*nb + t*B + i], i < B, as one aligned vector.
 template <int B>
 __device__ __forceinline__ void build_table(float* tab, const Args& a, int nb) {
   const Geometry& g = a.g;
@@ -123,7 +204,7 @@ __device__ __forceinline__ void build_table(float* tab, const Args& a, int nb) {
   }
 }
 
-// Per-visibility record: meta = {qu | qv<<16, rqu | rqv<<16, table offset u, table offset v}.
+// Per-visibility record: meta = {qu | qv<<16, 4*rqu | (4*rqv)<<16, table offset u, table offset v}.
 //  - q: block index of the box origin (footprint start / B).
 //  - rq: q mod n, the thread position that holds the box's first block.
 //  - table offsets select (row, phase) in the padded tables.
@@ -142,7 +223,7 @@ __device__ __forceinline__ bool make_meta(const Args& a, double2 x, int4& meta) 
   const int qu = cu0 / BU, remu = cu0 - qu * BU;
   const int qv = cv0 / BV, remv = cv0 - qv * BV;
   const int rqu = qu % g.nu, rqv = qv % g.nv;
-  meta = make_int4(qu | (qv << 16), rqu | (rqv << 16), (ru * BU + remu) * g.nbu, (rv * BV + remv) * g.nbv);
+  meta = make_int4(qu | (qv << 16), (rqu << 2) | (rqv << 18), (ru * BU + remu) * g.nbu, (rv * BV + remv) * g.nbv);
   return true;
 }
 
@@ -271,32 +352,32 @@ __host__ __device__ inline SmemLayout degrid_layout(const Geometry& g, int nthre
 
 // Flush one block of register accumulators to the grid in global memory with
 // vector atomic adds, then zero them. Cells past the grid's high edge (the
-// box can overhang it) hold exact zeros and are not written. All-zero
-// vectors are skipped.
+// box can overhang it) hold exact zeros and are not written. Row pointers are
+// stepped, not recomputed. There is no per-vector zero test: with B <= 3 no
+// block lies wholly in the padding, and with larger B such a block only adds
+// zeros (one wasted atomic), which is cheaper than testing every vector.
 template <int BU, int BV, int P>
 __device__ __forceinline__ void flush_global(float2 (&acc)[P][BV][BU], unsigned key, float2* __restrict__ grid, int G) {
   const int u0 = (int)(key & 0xFFFFu) * BU;
   const int v0 = (int)(key >> 16) * BV;
+  const size_t plane = (size_t)G * G;
+  float2* base = grid + (size_t)v0 * G + u0;
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
+  for (int j = 0; j < BV; ++j) {
+    const bool vin = v0 + j < G;
 #pragma unroll
-    for (int j = 0; j < BV; ++j) {
-      const int v = v0 + j;
-      float2* row = grid + ((size_t)p * G + v) * G + u0;
+    for (int p = 0; p < P; ++p) {
+      float2* row = base + p * plane + (size_t)j * G;
       if constexpr (BU % 2 == 0) {
 #pragma unroll
         for (int i = 0; i < BU; i += 2) {
-          const float4 q = make_float4(acc[p][j][i].x, acc[p][j][i].y, acc[p][j][i + 1].x, acc[p][j][i + 1].y);
-          const bool nz = (q.x != 0.f) | (q.y != 0.f) | (q.z != 0.f) | (q.w != 0.f);
-          if (nz && v < G && u0 + i + 1 < G) atomicAdd((float4*)(row + i), q);
+          if (vin && u0 + i + 1 < G)
+            atomicAdd((float4*)(row + i), make_float4(acc[p][j][i].x, acc[p][j][i].y, acc[p][j][i + 1].x, acc[p][j][i + 1].y));
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < BU; ++i) {
-          const float2 q = acc[p][j][i];
-          const bool nz = (q.x != 0.f) | (q.y != 0.f);
-          if (nz && v < G && u0 + i < G) atomicAdd(row + i, q);
-        }
+        for (int i = 0; i < BU; ++i)
+          if (vin && u0 + i < G) atomicAdd(row + i, acc[p][j][i]);
       }
 #pragma unroll
       for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
@@ -383,6 +464,42 @@ __device__ __forceinline__ void window_flush(bool need, unsigned key, float2 (&a
     // the last warp of a CTA whose size is not a multiple of 32 has fewer
     // lanes (wmask holds the low ones), so the stride is the lane count
     const int nl = __popc(w.wmask);
+    constexpr bool kSmallF = F <= 32 && 32 % F == 0;
+    constexpr bool kBigF = F % 32 == 0 && F > 32;
+    if ((kSmallF || kBigF) && nl == 32) {
+      // Fast path: element e of every slot always lands at the same offset
+      // from the slot's block origin, so each lane's offsets are fixed.
+      if constexpr (kSmallF) {
+        const int e = lane % F;
+        const int c = e & 1, q = e >> 1;
+        const int eoff = (q / (BU * BV)) * w.ps + ((q / BU) % BV) * w.ws + 2 * (q % BU) + c;
+        for (int sl = lane / F; sl < cnt; sl += 32 / F) {
+          const float v = w.slots[sl * F + e];
+          if (v != 0.f) {
+            const unsigned k2 = w.keys[sl];
+            const int base = ((int)(k2 >> 16) * BV - w.wv0) * w.ws + 2 * ((int)(k2 & 0xFFFFu) * BU - w.wu0);
+            atomicAdd(w.buf + base + eoff, v);
+          }
+        }
+      } else if constexpr (kBigF) {
+        int eoff[F / 32 > 0 ? F / 32 : 1];
+#pragma unroll
+        for (int t = 0; t < F / 32; ++t) {
+          const int e = lane + 32 * t;
+          const int c = e & 1, q = e >> 1;
+          eoff[t] = (q / (BU * BV)) * w.ps + ((q / BU) % BV) * w.ws + 2 * (q % BU) + c;
+        }
+        for (int sl = 0; sl < cnt; ++sl) {
+          const unsigned k2 = w.keys[sl];
+          const int base = ((int)(k2 >> 16) * BV - w.wv0) * w.ws + 2 * ((int)(k2 & 0xFFFFu) * BU - w.wu0);
+#pragma unroll
+          for (int t = 0; t < F / 32; ++t) {
+            const float v = w.slots[sl * F + lane + 32 * t];
+            if (v != 0.f) atomicAdd(w.buf + base + eoff[t], v);
+          }
+        }
+      }
+    } else
     for (int idx = lane; idx < cnt * F; idx += nl) {
       const int s = idx / F;
       const int e = idx - s * F;
@@ -430,9 +547,11 @@ __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long 
   }
 }
 
+// The thread's block inside the box: position t = (a - rq) mod n per axis,
+// block index q + t (the record stores 4*rq).
 __device__ __forceinline__ unsigned box_key(const int4 m, int au, int av, const Geometry& g, int& tu, int& tv) {
   const int qu = m.x & 0xFFFF, qv = (int)((unsigned)m.x >> 16);
-  const int rqu = m.y & 0xFFFF, rqv = (int)((unsigned)m.y >> 16);
+  const int rqu = (m.y & 0xFFFF) >> 2, rqv = (int)((unsigned)m.y >> 18);
   tu = au - rqu;
   tu += (tu < 0) ? g.nu : 0;
   tv = av - rqv;
@@ -545,6 +664,7 @@ __global__ void grid_kernel(Args a) {
   } else {
   // ---- patch schedule
   __shared__ int s_item;
+  __shared__ int s_next;  // next unclaimed chunk of the current item (warp_sync mode)
   __shared__ int s_dirty[4];
   WindowCtx w;
   w.buf = (float*)(smem + L.win);
@@ -562,6 +682,7 @@ __global__ void grid_kernel(Args a) {
     __syncthreads();  // previous item flushed, window zero, tables ready
     if (threadIdx.x == 0) {
       s_item = atomicAdd(a.work_next, 1);
+      s_next = 0;
       s_dirty[0] = a.win; s_dirty[1] = a.win; s_dirty[2] = 0; s_dirty[3] = 0;
     }
     __syncthreads();
@@ -572,9 +693,24 @@ __global__ void grid_kernel(Args a) {
     w.wv0 = wk.y;
     int4 dirty = make_int4(a.win, a.win, 0, 0);
     const int n_item_chunks = wk.w - wk.z;
-    const int rounds = (n_item_chunks + g.tpc - 1) / g.tpc;
+    // Warp-synchronous teams claim chunks a warp at a time from a shared
+    // counter, so a warp with nothing left to do leaves at once. Otherwise all
+    // teams of the CTA step through rounds together.
+    const int lane_id = threadIdx.x & 31;
+    const int tpw = __popc(wmask) / g.ts;           // teams in this warp (warp_sync mode)
+    const int team_in_warp = lane_id / g.ts;
+    const int rounds = a.warp_sync ? 0x7FFFFFFF : (n_item_chunks + g.tpc - 1) / g.tpc;
     for (int rd = 0; rd < rounds; ++rd) {
-      const int ci = rd * g.tpc + team;
+      int ci;
+      if (a.warp_sync) {
+        int base = 0;
+        if (lane_id == 0) base = atomicAdd(&s_next, tpw);
+        base = __shfl_sync(wmask, base, 0);
+        if (base >= n_item_chunks) break;
+        ci = base + team_in_warp;
+      } else {
+        ci = rd * g.tpc + team;
+      }
       long long vbeg = 0, vend = 0;
       if (ci < n_item_chunks) {
         const long long chunk = a.chunk_order[wk.z + ci];
@@ -629,7 +765,7 @@ __global__ void grid_kernel(Args a) {
         if (nz) {
           const int gu = w.wu0 + lu, gv = w.wv0 + vv;
           if (gu >= 0 && gv >= 0 && gu + 1 < g.G && gv < g.G)
-            atomicAdd((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
+            red_keep((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
           *src = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
@@ -659,7 +795,7 @@ __device__ __forceinline__ void load_block(float2 (&gb)[P][BV][BU], unsigned key
 #pragma unroll
         for (int i = 0; i < BU; i += 2) {
           float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (v < G && u0 + i + 1 < G) q = __ldg((const float4*)(row + i));
+          if (v < G && u0 + i + 1 < G) q = ld_keep((const float4*)(row + i));
           gb[p][j][i] = make_float2(q.x, q.y);
           gb[p][j][i + 1] = make_float2(q.z, q.w);
         }
@@ -667,7 +803,7 @@ __device__ __forceinline__ void load_block(float2 (&gb)[P][BV][BU], unsigned key
 #pragma unroll
         for (int i = 0; i < BU; ++i) {
           float2 q = make_float2(0.f, 0.f);
-          if (v < G && u0 + i < G) q = __ldg(row + i);
+          if (v < G && u0 + i < G) q = ld_keep(row + i);
           gb[p][j][i] = q;
         }
       }
@@ -709,7 +845,7 @@ __global__ void degrid_kernel(Args a) {
       const long long k = vbeg + (long long)b * kRBD + r;
       int4 m;
       m.x = (int)kInvalid;
-      if (k < vend && !make_meta<BU, BV>(a, a.uv[k], m)) atomicAdd(a.skipped, 1ULL);
+      if (k < vend && !make_meta<BU, BV>(a, ld_stream(a.uv + k), m)) atomicAdd(a.skipped, 1ULL);
       mtb[r] = m;
     }
     group_sync(a, wmask);
@@ -755,8 +891,8 @@ __global__ void degrid_kernel(Args a) {
         const float* col = red + (size_t)o * tsp;
         float sum = 0.f;
         for (int t = 0; t < g.ts; ++t) sum += col[t];
-        if (a.weights) sum *= a.weights[k];
-        ((float*)a.vis_out)[k * 2 * P + (o - r * 2 * P)] = sum;
+        if (a.weights) sum *= ld_stream(a.weights + k);
+        st_stream((float*)a.vis_out + k * 2 * P + (o - r * 2 * P), sum);
       }
     }
     // the next batch stages into the other meta buffer; its group_sync
@@ -883,7 +1019,7 @@ __global__ void grid_batch_kernel(BatchArgs b) {
     const int l = threadIdx.x - team * g.ts;
     const bool active = team < u.z;  // u.z <= tpc chunks in this unit
     const int au = l % g.nu, av = l / g.nu;
-    const long long chunk = (long long)u.y + team;
+      const long long chunk = (long long)u.y + team;
     const long long vbeg = chunk * b.chunk_len;
     const long long vend = active ? min(vbeg + b.chunk_len, it.n_vis) : vbeg;
     int4* const mt0 = meta + team * kRB;
