@@ -310,6 +310,16 @@ __host__ __device__ inline int win_plane_stride(int win) {
   return x + ((8 - x % 32) + 32) % 32;
 }
 
+// Degridding team reduction buffer. Thread t of a team stores the 2P partial
+// sums of record r contiguously at r*R + t*2P. The record stride R is padded
+// to 8 (mod 32) floats and the team stride by 16 more, so that both the
+// stores and the group reads below spread over the banks.
+__host__ __device__ inline int degrid_rec_stride(int ts, int P) {
+  const int x = ts * 2 * P;
+  return x + ((8 - x % 32) + 32) % 32;
+}
+__host__ __device__ inline int degrid_team_stride(int ts, int P) { return kRBD * degrid_rec_stride(ts, P) + 16; }
+
 struct SmemLayout {
   size_t tabU, tabV, meta, vals, win, slots, keys, red, total;
 };
@@ -340,7 +350,8 @@ __host__ __device__ inline SmemLayout degrid_layout(const Geometry& g, int nthre
   L.tabU = off; off += align16((size_t)g.O * BU * g.nbu * 4);
   L.tabV = off; off += align16((size_t)g.O * BV * g.nbv * 4);
   L.meta = off; off += align16((size_t)2 * g.tpc * kRBD * 16);
-  L.red = off; off += align16((size_t)g.tpc * kRBD * 2 * P * tsp * 4);
+  L.red = off; off += align16((size_t)g.tpc * degrid_team_stride(g.ts, P) * 4);
+  (void)tsp;
   (void)nthreads;
   (void)win;
   L.total = off;
@@ -819,7 +830,6 @@ __global__ void degrid_kernel(Args a) {
   float* tabU = (float*)(smem + L.tabU);
   float* tabV = (float*)(smem + L.tabV);
   int4* meta = (int4*)(smem + L.meta);
-  const int tsp = g.ts | 1;
 
   build_table<BU>(tabU, a, g.nbu);
   build_table<BV>(tabV, a, g.nbv);
@@ -833,7 +843,8 @@ __global__ void degrid_kernel(Args a) {
   const long long vend = chunk < a.n_chunks ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
   int4* const mt0 = meta + team * kRBD;
   int4* const mt1 = meta + (g.tpc + team) * kRBD;
-  float* red = (float*)(smem + L.red) + (size_t)team * kRBD * 2 * P * tsp;
+  const int R = degrid_rec_stride(g.ts, P);
+  float* red = (float*)(smem + L.red) + (size_t)team * degrid_team_stride(g.ts, P);
   const int nb = (a.chunk_len + kRBD - 1) / kRBD;
 
   float2 gb[P][BV][BU];
@@ -876,23 +887,49 @@ __global__ void degrid_kernel(Args a) {
           }
         }
       }
+      float* dst = red + r * R + l * 2 * P;
+      if constexpr (P % 2 == 0) {
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        red[(r * 2 * P + 2 * p) * tsp + l] = s[p].x;
-        red[(r * 2 * P + 2 * p + 1) * tsp + l] = s[p].y;
+        for (int p = 0; p < P; p += 2) *(float4*)(dst + 2 * p) = make_float4(s[p].x, s[p].y, s[p + 1].x, s[p + 1].y);
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) *(float2*)(dst + 2 * p) = s[p];
       }
     }
     group_sync(a, wmask);
-    // each team thread sums whole columns: output o = (record, component)
-    for (int o = l; o < kRBD * 2 * P; o += g.ts) {
-      const int r = o / (2 * P);
-      const long long k = vbeg + (long long)b * kRBD + r;
-      if (k < vend) {
-        const float* col = red + (size_t)o * tsp;
-        float sum = 0.f;
-        for (int t = 0; t < g.ts; ++t) sum += col[t];
-        if (a.weights) sum *= ld_stream(a.weights + k);
-        st_stream((float*)a.vis_out + k * 2 * P + (o - r * 2 * P), sum);
+    // Each team thread reduces whole groups of components over the team:
+    // 4 components (2 complex values) per group when P >= 2, else 2.
+    {
+      constexpr int QW = (P % 2 == 0) ? 4 : 2;
+      constexpr int GPR = 2 * P / QW;
+      for (int gi = l; gi < kRBD * GPR; gi += g.ts) {
+        const int r = gi / GPR;
+        const int q = gi - r * GPR;
+        const long long k = vbeg + (long long)b * kRBD + r;
+        if (k >= vend) continue;
+        const float* col = red + r * R + q * QW;
+        float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+        for (int t = 0; t < g.ts; ++t) {
+          if constexpr (QW == 4) {
+            const float4 v4 = *(const float4*)(col + t * 2 * P);
+            s0 = __fadd2_rn(s0, make_float2(v4.x, v4.y));
+            s1 = __fadd2_rn(s1, make_float2(v4.z, v4.w));
+          } else {
+            s0 = __fadd2_rn(s0, *(const float2*)(col + t * 2 * P));
+          }
+        }
+        if (a.weights) {
+          const float wk = ld_stream(a.weights + k);
+          s0 = make_float2(s0.x * wk, s0.y * wk);
+          s1 = make_float2(s1.x * wk, s1.y * wk);
+        }
+        float* out = (float*)a.vis_out + k * 2 * P + q * QW;
+        st_stream(out, s0.x);
+        st_stream(out + 1, s0.y);
+        if constexpr (QW == 4) {
+          st_stream(out + 2, s1.x);
+          st_stream(out + 3, s1.y);
+        }
       }
     }
     // the next batch stages into the other meta buffer; its group_sync
