@@ -51,6 +51,8 @@ def _load():
         lib.oracle_grid.restype = i64
         lib.oracle_degrid.argtypes = [i32, i32, i32, i32, i64, vp, vp, vp, vp]
         lib.oracle_degrid.restype = i64
+        lib.oracle_compress.argtypes = [i32, i32, i64, vp, vp, vp, vp, vp, vp]
+        lib.oracle_compress.restype = i64
         _lib = lib
     return _lib
 
@@ -132,3 +134,25 @@ def degrid(G: int, S: int, oversample: int, uv, grid_in, table):
     if r < 0:
         raise ValueError("bad arguments")
     return vis, int(r)
+
+
+def compress(oversample: int, uv, vis, weights=None):
+    """Merge runs of adjacent visibilities that share a fine position (compression, Sec. 2.2).
+
+    Returns ``(uv_out [m][2] float64, vis_out [m][P] complex128, run_of [n] int64)``. ``vis_out`` holds
+    the weighted sums; grid it with unit weights. ``run_of[k]`` is the merged record of visibility k.
+    """
+    uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(-1, 2)
+    n = uv.shape[0]
+    vis = np.ascontiguousarray(vis, dtype=np.complex128)
+    vis = vis if vis.ndim == 2 else vis.reshape(n, -1)
+    P = vis.shape[1]
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(n)
+    uv_out = np.empty((n, 2), np.float64)
+    vis_out = np.empty((n, P), np.complex128)
+    run_of = np.empty(n, np.int64)
+    m = _load().oracle_compress(oversample, P, n, _ptr(uv), _ptr(vis), None if w is None else _ptr(w),
+                                _ptr(uv_out), _ptr(vis_out), _ptr(run_of))
+    if m < 0:
+        raise ValueError("bad arguments")
+    return uv_out[:m].copy(), vis_out[:m].copy(), run_of

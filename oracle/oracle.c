@@ -235,3 +235,49 @@ int64_t oracle_degrid(int G, int S, int O, int P, int64_t n, const double* uv, c
   }
   return skipped;
 }
+
+/*
+ * Compression (Sec. 2.2, last paragraph; the scheme is Muscat's). Visibilities
+ * that are adjacent and sit on the same point of the oversampled grid meet
+ * the same GCF samples, so their weighted values can be added and gridded as
+ * one visibility. The grid is unchanged up to rounding.
+ * Readings:
+ *  - "adjacent" means consecutive in the given order. A run is a maximal
+ *    sequence of consecutive visibilities whose fine positions (f_u, f_v) are
+ *    equal. Equal fine positions on both axes mean the same cell and the same
+ *    GCF sample row.
+ *  - A visibility with no fine position is a run of its own. Such a run is
+ *    skipped when gridded, as before compression. A coordinate has no fine
+ *    position here when it is not finite or |u*O| >= 2^26. That is far
+ *    outside any supported grid (G <= 32768 and O <= 256 keep |u*O| < 2^22).
+ *  - A merged record carries the first member's uv and the sum over the run
+ *    of w_k V_k. Its weight is 1.
+ * Outputs: uv_out [m][2], vis_out [m][P] complex (interleaved), and run_of
+ * [n] (the run holding visibility k). Returns m, or -1 on bad arguments.
+ */
+int64_t oracle_compress(int O, int P, int64_t n, const double* uv, const double* vis, const double* weights,
+                        double* uv_out, double* vis_out, int64_t* run_of) {
+  if (!is_pow2(O) || P <= 0 || n < 0) return -1;
+  int64_t m = 0;
+  int prev_ok = 0;
+  int64_t pfu = 0, pfv = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t fu = 0, fv = 0;
+    int ok = oracle_fine_position(uv[2 * k], O, &fu) == 0 && oracle_fine_position(uv[2 * k + 1], O, &fv) == 0 &&
+             fabs(uv[2 * k] * (double)O) < 67108864.0 && fabs(uv[2 * k + 1] * (double)O) < 67108864.0;
+    int same = ok && prev_ok && fu == pfu && fv == pfv;
+    if (!same) {
+      uv_out[2 * m] = uv[2 * k];
+      uv_out[2 * m + 1] = uv[2 * k + 1];
+      for (int p = 0; p < 2 * P; ++p) vis_out[(size_t)m * 2 * P + p] = 0.0;
+      ++m;
+    }
+    double w = weights ? weights[k] : 1.0;
+    for (int p = 0; p < 2 * P; ++p) vis_out[(size_t)(m - 1) * 2 * P + p] += w * vis[(size_t)k * 2 * P + p];
+    run_of[k] = m - 1;
+    prev_ok = ok;
+    pfu = fu;
+    pfv = fv;
+  }
+  return m;
+}

@@ -69,6 +69,11 @@ def antenna_layout(n_ant: int, radius_m: float, rng: np.random.Generator) -> np.
     return np.stack([r * np.cos(a), r * np.sin(a), np.zeros(n_ant)], axis=1)
 
 
+def cored_layout(n_core: int, r_core_m: float, n_outer: int, r_outer_m: float, rng: np.random.Generator) -> np.ndarray:
+    """ENU positions of a dense core (n_core antennas in a disk of r_core_m) plus n_outer out to r_outer_m."""
+    return np.concatenate([antenna_layout(n_core, r_core_m, rng), antenna_layout(n_outer, r_outer_m, rng)])
+
+
 def baseline_pairs(n_ant: int) -> np.ndarray:
     """All (p, q) with p < q, in (p, q) order. Shape [n_ant*(n_ant-1)/2, 2]."""
     p, q = np.triu_indices(n_ant, k=1)
@@ -107,10 +112,14 @@ def gaussian_values(rng: np.random.Generator, n: int, npol: int) -> np.ndarray:
 
 
 def observation(name: str, G: int, S: int, oversample: int, npol: int, n_ant: int, radius_m: float,
-                n_times: int, n_chan: int, seed: int = 0, limit: int | None = None) -> Workload:
-    """A baseline-ordered observation: n_bl x n_times x n_chan samples (channel fastest)."""
+                n_times: int, n_chan: int, seed: int = 0, limit: int | None = None, layout=None) -> Workload:
+    """A baseline-ordered observation: n_bl x n_times x n_chan samples (channel fastest).
+
+    ``layout(rng)`` returns the ENU antenna positions; the default is n_ant uniform in a disk of radius_m.
+    """
     rng = np.random.default_rng(seed)
-    enu = antenna_layout(n_ant, radius_m, rng)
+    enu = antenna_layout(n_ant, radius_m, rng) if layout is None else layout(rng)
+    assert enu.shape == (n_ant, 3)
     uv = scale_to_grid(uv_tracks_m(enu, n_times, n_chan), G, S).reshape(-1, 2)
     if limit is not None:
         uv = np.ascontiguousarray(uv[:limit])
@@ -139,6 +148,16 @@ def precision_single_pol(seed: int = 0) -> Workload:
 def differentiation(seed: int = 0) -> Workload:
     """G=1024, S=7, O=8, P=1; 64 antennas; the first 1,000,000 of 2016 bl x 497 t."""
     return observation("diff G1024 S7 O8 P1 1000000vis", 1024, 7, 8, 1, 64, 4000.0, 497, 1, seed, limit=1_000_000)
+
+
+def cored_quad_pol(seed: int = 0) -> Workload:
+    """G=2048, S=7, O=8, P=4; 48 antennas in a 300 m core plus 16 out to 8 km; 2016 bl x 1024 t x 4 ch.
+
+    The short core baselines put runs of adjacent samples on one oversampled-grid point, so compression
+    (merging such runs) removes about 44% of the 8,257,536 records.
+    """
+    return observation("cored-quad-pol G2048 S7 O8 P4 8257536vis", 2048, 7, 8, 4, 64, 8000.0, 1024, 4, seed,
+                       layout=lambda rng: cored_layout(48, 300.0, 16, 8000.0, rng))
 
 
 def scaled_down(w: Workload, n: int) -> Workload:
