@@ -47,12 +47,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="auto", help="grid plan: auto | chunked:Bu,Bv | patch:Bu,Bv")
+    ap.add_argument("--config", default="auto", help="grid plan: auto | chunked:Bu,Bv[:vis_per_chunk] | patch:Bu,Bv[:vis_per_chunk]")
     ap.add_argument("--degrid-config", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--vis", type=int, default=0, help="use only the first N visibilities (profiling runs)")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain Romein kernel (profiling runs)")
+    ap.add_argument("--no-compression", action="store_true", help="skip the compression measurement")
     return ap.parse_args()
 
 
@@ -188,10 +189,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_compression(gb, autotune, torch, dev, cfg_grid, cfg_degrid, steps, warmup, seed):
+    """Grid + degrid step on the cored quad-pol workload with and without compression (Sec. 2.2).
+
+    The compressed step is compress -> grid(merged) -> degrid(merged) -> expand to every original
+    visibility: the same results as the plain step, up to rounding. Rates count ORIGINAL
+    visibility-taps, so the two are directly comparable.
+    """
+    w = synth.cored_quad_pol(seed=seed)
+    S2 = w.S * w.S
+    stream = torch.cuda.current_stream()
+    uv = torch.from_numpy(w.uv).to(dev)
+    vis = torch.from_numpy(w.vis).to(dev)
+    wt = torch.from_numpy(w.weights).to(dev)
+    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta, device=dev)
+    gplan = gb.Plan(w.G, w.S, w.oversample, w.npol, **autotune.plan_kwargs(cfg_grid))
+    dplan = gb.Plan(w.G, w.S, w.oversample, w.npol, **autotune.plan_kwargs(cfg_degrid))
+    g = torch.zeros((w.npol, w.G, w.G), dtype=torch.complex64, device=dev)
+    vis_out = torch.empty((w.n_vis, w.npol), dtype=torch.complex64, device=dev)
+    bufs = (torch.empty((w.n_vis, 2), dtype=torch.float64, device=dev),
+            torch.empty((w.n_vis, w.npol), dtype=torch.complex64, device=dev),
+            torch.empty(w.n_vis, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+    dc = torch.empty((w.n_vis, w.npol), dtype=torch.complex64, device=dev)
+    gb.grid_compress(gplan, uv, vis, wt, out=bufs, sync=False)
+    m = int(bufs[3].item())  # a deterministic function of the inputs; read once, outside the timed steps
+    uv_c, vis_c, run_of = bufs[0][:m], bufs[1][:m], bufs[2]
+
+    def plain(ev):
+        g.zero_()
+        ev[0].record(stream)
+        gb.grid(gplan, uv, vis, wt, table, g)
+        gb.degrid(dplan, uv, g, table, vis_out)
+        ev[1].record(stream)
+
+    def compressed(ev):
+        g.zero_()
+        ev[0].record(stream)
+        gb.grid_compress(gplan, uv, vis, wt, out=bufs, sync=False)
+        ev[2].record(stream)
+        gb.grid(gplan, uv_c, vis_c, None, table, g)
+        gb.degrid(dplan, uv_c, g, table, dc[:m])
+        ev[3].record(stream)
+        gb.degrid_expand(dplan, run_of, dc[:m], None, vis_out)
+        ev[1].record(stream)
+
+    def run(fn):
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(warmup + steps)]
+        for ev in evs:
+            fn(ev)
+        torch.cuda.synchronize()
+        evs = evs[warmup:]
+        tot = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+        parts = None
+        if fn is compressed:
+            parts = (float(np.mean([e[0].elapsed_time(e[2]) for e in evs])),
+                     float(np.mean([e[3].elapsed_time(e[1]) for e in evs])))
+        return tot, parts
+
+    t0, _ = run(plain)
+    t1, (tc, te) = run(compressed)
+    taps = 2.0 * w.n_vis * S2
+    return {"workload": "cored quad-pol: G=2048 S=7 O=8 P=4, 48 antennas in a 300 m core + 16 out to 8 km, "
+                        "2016 bl x 1024 t x 4 ch = 8,257,536 vis",
+            "n_vis": w.n_vis, "n_compressed": m, "ratio": w.n_vis / m,
+            "ms_per_step_uncompressed": t0, "ms_per_step_compressed": t1, "compress_ms": tc, "expand_ms": te,
+            "value_uncompressed": taps / (t0 / 1e3), "value_compressed": taps / (t1 / 1e3),
+            "unit": "original vis-taps/s (grid + degrid)"}
+
+
 def parse_cfg(s):
-    sched, b = s.split(":")
-    bu, bv = (int(x) for x in b.split(","))
-    return sched, bu, bv
+    """'chunked:Bu,Bv' or 'chunked:Bu,Bv:L' (L visibilities per chunk) -> plan config dict."""
+    parts = s.split(":")
+    bu, bv = (int(x) for x in parts[1].split(","))
+    cfg = dict(schedule=parts[0], Bu=bu, Bv=bv)
+    if len(parts) > 2:
+        cfg["vis_per_chunk"] = int(parts[2])
+    return cfg
 
 
 def main():
@@ -226,13 +299,11 @@ def main():
     if args.config == "auto":
         best_grid = autotune.tune_grid(w, uv, vis, wt, table, grid_buf, reps=2)
     else:
-        s, bu, bv = parse_cfg(args.config)
-        best_grid = dict(schedule=s, Bu=bu, Bv=bv)
+        best_grid = parse_cfg(args.config)
     if args.degrid_config == "auto":
         best_degrid = autotune.tune_degrid(w, uv, table, grid_buf, vis_out, reps=2)
     else:
-        s, bu, bv = parse_cfg(args.degrid_config)
-        best_degrid = dict(schedule=s, Bu=bu, Bv=bv)
+        best_degrid = parse_cfg(args.degrid_config)
     gplan = gb.Plan(w.G, w.S, w.oversample, w.npol, **autotune.plan_kwargs(best_grid))
     dplan = gb.Plan(w.G, w.S, w.oversample, w.npol, **autotune.plan_kwargs(best_degrid))
     pplan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=1, vis_per_chunk=1024, schedule="chunked")
@@ -349,13 +420,19 @@ def main():
         cpu = {"value": float(np.mean(rates)), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"all {w.n_vis} visibilities x {len(rates)}, grid + degrid, FP64, 1 thread ({spent:.1f} s)"}
 
+    comp = None
+    if not args.no_compression and not args.vis:
+        comp = measure_compression(gb, autotune, torch, dev, best_grid, best_degrid, args.steps, args.warmup,
+                                   sharding.rank_seed(0, rank))
+
     launches_per_step = (4 if best_grid["schedule"] == "patch" else 1) + 1
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded earth-rotation uv tracks, complex Gaussian values; stand-in for the paper's MeerKAT set)",
-            "config": {"workload": WORKLOAD, "grid_plan": best_grid, "degrid_plan": best_degrid,
+            "config": {"workload": WORKLOAD if not args.vis else f"{WORKLOAD}, cut to the first {w.n_vis:,}",
+                       "grid_plan": best_grid, "degrid_plan": best_degrid,
                        "cache": "inputs (429 MB) larger than L2 (129 MB); grid zeroed inside each step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "grid_ms": g_ms, "degrid_ms": d_ms,
@@ -376,6 +453,8 @@ def main():
             line["e2e"] = e2e
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if comp is not None:
+            line["compression"] = comp
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

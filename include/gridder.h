@@ -166,7 +166,48 @@ int grid_compute_indices(grid_plan_t plan, int64_t n_vis, const double* uv, int3
 int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
 
 /*
- * Batched gridding (NEXT-2 in the design notes): many grids of the same side
+ * Compression (Sec. 2.2, last paragraph, after Muscat): adjacent visibilities
+ * that fall on the same point of the oversampled grid meet the same GCF
+ * samples, so their weighted values can be added and gridded as one
+ * visibility. The grid is unchanged up to FP32 rounding.
+ *  - A run is a maximal sequence of consecutive visibilities (in the given
+ *    order) whose fine positions floor(u*O + 1/2), floor(v*O + 1/2) are equal
+ *    on both axes: the same cell and the same GCF sample row. A visibility
+ *    whose coordinate is not finite or has |u*O| >= 2^26 (far off any
+ *    supported grid) is a run of its own.
+ *  - Run m gets uv_out[m] = uv of its first member and vis_out[m][p] = the sum
+ *    over its members, in input order, of w_k * vis[k][p] (FP32). Grid the
+ *    output with weights = NULL and an FP32 plan of the same G, S, O and
+ *    npol: vis_out is complex64 whatever the plan's precision.
+ *  - run_of[k] (optional, may be NULL) = the run holding visibility k.
+ *  - *n_out = the number of runs, written on the stream (n_out is a DEVICE
+ *    pointer to one int64; read it after the stream work completes).
+ * Inputs as for grid(): uv [n][2] f64, vis [n][npol] in the plan precision,
+ * weights [n] f32 or NULL. Outputs are caller-allocated device buffers with
+ * room for n_vis runs: uv_out [n][2] f64 (16-byte aligned), vis_out [n][npol]
+ * complex64, run_of [n] int64. The plan keeps a scratch buffer of about
+ * n_vis/8 bytes, allocated on the first call that needs more (synchronous
+ * cudaMalloc). Returns GRID_OK, GRID_ERR_INVALID, GRID_ERR_NOMEM or
+ * GRID_ERR_CUDA.
+ */
+int grid_compress(grid_plan_t plan, int64_t n_vis, const double* uv, const void* vis, const float* weights,
+                  double* uv_out, void* vis_out, int64_t* run_of, int64_t* n_out, cudaStream_t stream);
+
+/*
+ * Expansion after degridding compressed records: every member of a run has
+ * the run's fine position, so its degridded value is the run's.
+ *   vis_out[k][p] = w_k * vis_compressed[run_of[k]][p]   (w_k = 1 if weights is NULL)
+ * run_of [n] int64 comes from grid_compress() on the same n visibilities;
+ * vis_compressed is complex64 [n_compressed][npol] (for example from degrid()
+ * on the compressed uv). A run index outside [0, n_compressed) gives 0.
+ * OVERWRITES vis_out (complex64 [n][npol]). Device pointers; with even npol,
+ * vis_compressed and vis_out must be 16-byte aligned.
+ */
+int degrid_expand(grid_plan_t plan, int64_t n_vis, const int64_t* run_of, int64_t n_compressed,
+                  const void* vis_compressed, const float* weights, void* vis_out, cudaStream_t stream);
+
+/*
+ * Batched gridding: many grids of the same side
  * G, oversampling O and polarization count, for example every
  * (channel, w-plane) of an observation (Sec. 5 grids each w-slice with its
  * own kernel instance). Each item has its own visibilities, GCF support S

@@ -167,6 +167,56 @@ def degrid_weighted(plan: Plan, uv, grid_in, kernel_table, weights, vis_out=None
     return vis_out
 
 
+def grid_compress(plan: Plan, uv, vis, weights=None, stream=None, out=None, sync: bool = True):
+    """grid_compress(): merge runs of adjacent visibilities on one oversampled-grid point.
+
+    Returns ``(uv_c [m, 2] float64, vis_c [m, P] complex64, run_of [n] int64)``. ``vis_c`` holds the
+    weighted sums (grid it with weights=None and an FP32 plan); ``run_of[k]`` is the run of visibility k.
+    Reading the run count m back synchronises with the stream. ``out`` = (uv_c, vis_c, run_of, n_out)
+    supplies the full-size output buffers. With ``sync=False`` nothing is read back: the call returns
+    the untrimmed buffers and the device tensor n_out holding m.
+    """
+    torch = _torch()
+    n = uv.shape[0]
+    pu = _dptr(uv, "uv", torch.float64, 2)
+    pv = _dptr(vis, "vis", _vis_dtype(plan))
+    pw = _dptr(weights, "weights", torch.float32, 1)
+    if vis.shape[0] != n or (weights is not None and weights.shape[0] != n):
+        raise ValueError("uv, vis and weights must have the same length")
+    if out is None:
+        out = (torch.empty((n, 2), dtype=torch.float64, device=uv.device),
+               torch.empty((n, plan.npol), dtype=torch.complex64, device=uv.device),
+               torch.empty(n, dtype=torch.int64, device=uv.device),
+               torch.zeros(1, dtype=torch.int64, device=uv.device))
+    uv_c, vis_c, run_of, n_out = out
+    if uv_c.shape[0] < n or vis_c.shape[0] < n or run_of.shape[0] < n:
+        raise ValueError("output buffers need room for n records")
+    _lib.check(_lib.load().grid_compress(plan.handle, n, pu, pv, pw or None, _dptr(uv_c, "uv_c", torch.float64, 2),
+                                         _dptr(vis_c, "vis_c", torch.complex64, 2), _dptr(run_of, "run_of", torch.int64, 1),
+                                         _dptr(n_out, "n_out", torch.int64, 1), _stream_ptr(stream)))
+    if not sync:
+        return uv_c, vis_c, run_of, n_out
+    m = int(n_out.item())
+    return uv_c[:m], vis_c[:m], run_of[:n]
+
+
+def degrid_expand(plan: Plan, run_of, vis_c, weights=None, vis_out=None, stream=None):
+    """degrid_expand(): vis_out[k] = w_k * vis_c[run_of[k]] (the degridded value of each merged record's members)."""
+    torch = _torch()
+    n = run_of.shape[0]
+    if vis_out is None:
+        vis_out = torch.empty((n, plan.npol), dtype=torch.complex64, device=run_of.device)
+    pr = _dptr(run_of, "run_of", torch.int64, 1)
+    pc = _dptr(vis_c, "vis_c", torch.complex64, 2) if vis_c.shape[0] > 0 else 0
+    pw = _dptr(weights, "weights", torch.float32, 1)
+    po = _dptr(vis_out, "vis_out", torch.complex64, 2)
+    if weights is not None and weights.shape[0] != n:
+        raise ValueError("weights must have one entry per visibility")
+    _lib.check(_lib.load().degrid_expand(plan.handle, n, pr, int(vis_c.shape[0]), pc or None, pw or None, po,
+                                         _stream_ptr(stream)))
+    return vis_out
+
+
 def grid_make_kernel_table(S: int, oversample: int, beta: float, precision: str = "f32", device=None, stream=None):
     """Oversampled Kaiser-Bessel table [O, S], computed on the device in FP64 and rounded once."""
     torch = _torch()

@@ -20,7 +20,7 @@ import numpy as np
 from . import synth
 
 BLOCK_CANDIDATES = [(1, 1), (2, 1), (1, 2), (2, 2), (4, 2), (2, 4), (3, 3), (4, 4), (8, 2), (2, 8)]
-CHUNKED_LENGTHS = (256, 1024)
+CHUNKED_LENGTHS = (128, 256, 1024)
 PATCH_LENGTHS = (32, 64)
 
 

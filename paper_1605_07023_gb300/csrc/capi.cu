@@ -26,6 +26,8 @@ struct grid_plan_s {
   unsigned long long* d_skipped;
   PatchScratch ps;
   long long ps_chunks_cap;  // chunk capacity of the patch scratch
+  void* cs_buf;             // compression scratch (grow-only)
+  size_t cs_bytes;
 };
 
 namespace {
@@ -161,11 +163,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   pl->k = k;
   Geometry& g = pl->g;
   g.G = d.G; g.S = d.S; g.O = d.oversample; g.log2O = ilog2(d.oversample); g.h = (d.S - 1) / 2; g.P = d.npol;
-  g.nbu = ((d.S + d.Bu - 1 + d.Bu - 1) / d.Bu) * d.Bu;
-  g.nbv = ((d.S + d.Bv - 1 + d.Bv - 1) / d.Bv) * d.Bv;
-  g.nu = g.nbu / d.Bu;
-  g.nv = g.nbv / d.Bv;
-  g.ts = g.nu * g.nv;
+  finish_geometry(g, d.Bu, d.Bv);
 
   cudaError_t e = cudaGetDevice(&pl->device);
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
@@ -256,6 +254,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
 void grid_plan_destroy(grid_plan_t pl) {
   if (!pl) return;
   free_patch(pl);
+  cudaFree(pl->cs_buf);
   cudaFree(pl->d_skipped);
   delete pl;
 }
@@ -385,6 +384,63 @@ int grid_plan_skipped(grid_plan_t pl, int64_t* n_skipped, int reset) {
     e = cudaMemset(pl->d_skipped, 0, sizeof v);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }
+  return GRID_OK;
+}
+
+int grid_compress(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const float* weights,
+                  double* uv_out, void* vis_out, int64_t* run_of, int64_t* n_out, cudaStream_t stream) {
+  g_err.clear();
+  if (!pl) return fail(GRID_ERR_INVALID, "null plan");
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
+  if (!n_out || !aligned(n_out, 8)) return fail(GRID_ERR_INVALID, "n_out must be a non-null 8-byte aligned device pointer");
+  int rc = check_device(pl);
+  if (rc) return rc;
+  if (n_vis == 0) {
+    cudaError_t e = cudaMemsetAsync(n_out, 0, sizeof(int64_t), stream);
+    return e == cudaSuccess ? GRID_OK : cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (!uv || !vis || !uv_out || !vis_out) return fail(GRID_ERR_INVALID, "null uv, vis, uv_out or vis_out");
+  if (!aligned(uv, 16) || !aligned(uv_out, 16)) return fail(GRID_ERR_INVALID, "uv and uv_out must be 16-byte aligned");
+  const size_t vbytes = (pl->desc.precision == GRID_PREC_F32 ? 8 : 4) * (size_t)pl->g.P;
+  if (!aligned(vis, vbytes >= 16 ? 16 : vbytes)) return fail(GRID_ERR_INVALID, "vis must be %zu-byte aligned", vbytes >= 16 ? (size_t)16 : vbytes);
+  if (!aligned(vis_out, 8)) return fail(GRID_ERR_INVALID, "vis_out must be 8-byte aligned");
+  if (weights && !aligned(weights, 4)) return fail(GRID_ERR_INVALID, "weights must be 4-byte aligned");
+  if (run_of && !aligned(run_of, 8)) return fail(GRID_ERR_INVALID, "run_of must be 8-byte aligned");
+  const size_t need = compress_scratch_bytes(n_vis, pl->g.P);
+  if (need > pl->cs_bytes) {
+    cudaFree(pl->cs_buf);
+    pl->cs_buf = nullptr;
+    pl->cs_bytes = 0;
+    cudaError_t e = cudaMalloc(&pl->cs_buf, need + need / 4);
+    if (e != cudaSuccess) return fail(GRID_ERR_NOMEM, "compression scratch allocation failed: %s", cudaGetErrorString(e));
+    pl->cs_bytes = need + need / 4;
+  }
+  Args a = make_args(pl, n_vis, uv);
+  a.vis = vis;
+  a.weights = weights;
+  cudaError_t e = launch_compress(a, pl->cs_buf, (double2*)uv_out, (float2*)vis_out, (long long*)run_of,
+                                  (long long*)n_out, pl->sm_count, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "compression kernel launch");
+  return GRID_OK;
+}
+
+int degrid_expand(grid_plan_t pl, int64_t n_vis, const int64_t* run_of, int64_t n_compressed, const void* vis_compressed,
+                  const float* weights, void* vis_out, cudaStream_t stream) {
+  g_err.clear();
+  if (!pl) return fail(GRID_ERR_INVALID, "null plan");
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
+  if (n_compressed < 0 || n_compressed > n_vis) return fail(GRID_ERR_INVALID, "n_compressed=%lld out of range", (long long)n_compressed);
+  if (n_vis == 0) return GRID_OK;
+  if (!run_of || !vis_out || (n_compressed > 0 && !vis_compressed)) return fail(GRID_ERR_INVALID, "null run_of, vis_compressed or vis_out");
+  const size_t va = pl->g.P % 2 == 0 ? 16 : 8;  // even P moves two complex values per vector access
+  if (!aligned(run_of, 8) || !aligned(vis_out, va) || (vis_compressed && !aligned(vis_compressed, va)))
+    return fail(GRID_ERR_INVALID, "run_of must be 8-byte, vis_compressed and vis_out %zu-byte aligned", va);
+  if (weights && !aligned(weights, 4)) return fail(GRID_ERR_INVALID, "weights must be 4-byte aligned");
+  int rc = check_device(pl);
+  if (rc) return rc;
+  cudaError_t e = launch_expand(pl->g.P, n_vis, (const long long*)run_of, n_compressed, (const float2*)vis_compressed,
+                                weights, (float2*)vis_out, pl->sm_count, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "expand kernel launch");
   return GRID_OK;
 }
 

@@ -35,4 +35,11 @@ cudaError_t launch_kb_table(int S, int O, double beta, int fmt, void* out, cudaS
 cudaError_t launch_indices(const Args& a, int32_t* cell, int32_t* sub, cudaStream_t st);
 cudaError_t launch_patch_binning(const Args& a, const PatchScratch& ps, cudaStream_t st);
 
+// Compression (compress.cu).
+size_t compress_scratch_bytes(long long n, int P);
+cudaError_t launch_compress(const Args& a, void* scratch, double2* uv_out, float2* vis_out, long long* run_of,
+                            long long* n_out, int sm_count, cudaStream_t st);
+cudaError_t launch_expand(int P, long long n, const long long* run_of, long long n_c, const float2* vis_c,
+                          const float* weights, float2* vis_out, int sm_count, cudaStream_t st);
+
 }  // namespace gbg

@@ -47,7 +47,30 @@ struct Geometry {
   int nu, nv;     // blocks per bin per axis
   int ts;         // team size nu*nv
   int tpc;        // teams per CTA
+  int nuB, nvB;   // nu*Bu, nv*Bv: a bin's width in table entries
+  unsigned mu, mv;  // floor(2^31/nu) + 1, floor(2^31/nv) + 1: exact division of block indices < 2^15
 };
+
+// Bin and team shape for blocks of Bu x Bv cells (Sec. 3): the bin is the
+// smallest multiple of the block that holds S + B - 1 cells per axis.
+__host__ __device__ inline void finish_geometry(Geometry& g, int BU, int BV) {
+  g.nbu = ((g.S + BU - 1 + BU - 1) / BU) * BU;
+  g.nbv = ((g.S + BV - 1 + BV - 1) / BV) * BV;
+  g.nu = g.nbu / BU;
+  g.nv = g.nbv / BV;
+  g.ts = g.nu * g.nv;
+  g.nuB = g.nu * BU;
+  g.nvB = g.nv * BV;
+  g.mu = (unsigned)((1ull << 31) / (unsigned)g.nu + 1);
+  g.mv = (unsigned)((1ull << 31) / (unsigned)g.nv + 1);
+}
+
+// q mod n for 0 <= q < 2^15, with m = floor(2^31/n) + 1: floor(q*m / 2^31) =
+// floor(q/n + q*e/2^31) with 0 < e <= 1, and q*e/2^31 < 2^-16 < 1/n, so the
+// quotient is exact.
+__device__ __forceinline__ int mod_small(int q, int n, unsigned m) {
+  return q - n * (int)__umulhi((unsigned)q << 1, m);
+}
 
 struct Args {
   Geometry g;
@@ -187,9 +210,13 @@ __device__ __forceinline__ float load_tap(const void* table, int fmt, int idx) {
   return ((const float*)table)[idx];
 }
 
+__device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
+
 // Zero-padded, phase-expanded 1-D tables: tab[(r*B + rem)*nb + k] = T[r][k - rem]
 // for 0 <= k - rem < S, else 0. A thread at block position t reads taps
-// tab[(r*B + rem)*nb + t*B + i], i < B, as one aligned vector.
+// tab[(r*B + rem)*nb + t*B + i], i < B, as one aligned vector. (Storing each
+// tap twice, as a ready (T, T) operand pair for the packed FMA, was measured
+// 3-12% slower: the doubled shared-memory loads cost more than the pairing.)
 template <int B>
 __device__ __forceinline__ void build_table(float* tab, const Args& a, int nb) {
   const Geometry& g = a.g;
@@ -204,10 +231,15 @@ __device__ __forceinline__ void build_table(float* tab, const Args& a, int nb) {
   }
 }
 
-// Per-visibility record: meta = {qu | qv<<16, 4*rqu | (4*rqv)<<16, table offset u, table offset v}.
-//  - q: block index of the box origin (footprint start / B).
-//  - rq: q mod n, the thread position that holds the box's first block.
-//  - table offsets select (row, phase) in the padded tables.
+// Per-visibility record, built once per visibility while staging, so that
+// each team thread needs only a few instructions per visibility:
+//  x = M = (qu - rqu) | (qv - rqv) << 16: the block index of the bin-aligned
+//      origin below the box (q = footprint start / B, rq = q mod n);
+//  y = rqu | rqv << 16: the thread position that holds the box's first block;
+//  z, w = table offset of (row, phase) minus rq*B, per axis.
+// Thread (au, av) owns block (b_u, b_v) = (M_u + au + [au < rqu]*nu, ...),
+// the one block of its residue class inside the box (Fig. 2), and reads its
+// taps at z + (au + [au < rqu]*nu)*Bu.
 template <int BU, int BV>
 __device__ __forceinline__ bool make_meta(const Args& a, double2 x, int4& meta) {
   const Geometry& g = a.g;
@@ -222,9 +254,37 @@ __device__ __forceinline__ bool make_meta(const Args& a, double2 x, int4& meta) 
   }
   const int qu = cu0 / BU, remu = cu0 - qu * BU;
   const int qv = cv0 / BV, remv = cv0 - qv * BV;
-  const int rqu = qu % g.nu, rqv = qv % g.nv;
-  meta = make_int4(qu | (qv << 16), (rqu << 2) | (rqv << 18), (ru * BU + remu) * g.nbu, (rv * BV + remv) * g.nbv);
+  const int rqu = mod_small(qu, g.nu, g.mu), rqv = mod_small(qv, g.nv, g.mv);
+  meta = make_int4((qu - rqu) | ((qv - rqv) << 16), rqu | (rqv << 16), (ru * BU + remu) * g.nbu - rqu * BU,
+                   (rv * BV + remv) * g.nbv - rqv * BV);
   return true;
+}
+
+// A thread's fixed place in its team.
+struct TeamPos {
+  int au, av;    // block position in the bin
+  unsigned A;    // au | av << 16
+  int ou, ov;    // au*Bu, av*Bv
+};
+
+template <int BU, int BV>
+__device__ __forceinline__ TeamPos team_pos(int l, const Geometry& g) {
+  TeamPos t;
+  t.au = l % g.nu;
+  t.av = l / g.nu;
+  t.A = (unsigned)t.au | ((unsigned)t.av << 16);
+  t.ou = t.au * BU;
+  t.ov = t.av * BV;
+  return t;
+}
+
+// The thread's block for record m (its key, u | v << 16) and its tap offsets.
+__device__ __forceinline__ unsigned box_key(const int4 m, const TeamPos& t, const Geometry& g, int& offu, int& offv) {
+  const bool wu = t.au < (m.y & 0xFFFF);
+  const bool wv = t.av < (int)((unsigned)m.y >> 16);
+  offu = m.z + t.ou + (wu ? g.nuB : 0);
+  offv = m.w + t.ov + (wv ? g.nvB : 0);
+  return (unsigned)m.x + t.A + (wu ? (unsigned)g.nu : 0u) + (wv ? ((unsigned)g.nv << 16) : 0u);
 }
 
 template <int P>
@@ -310,14 +370,21 @@ __host__ __device__ inline int win_plane_stride(int win) {
   return x + ((8 - x % 32) + 32) % 32;
 }
 
-// Degridding team reduction buffer. Thread t of a team stores the 2P partial
-// sums of record r contiguously at r*R + t*2P. The record stride R is padded
-// to 8 (mod 32) floats and the team stride by 16 more, so that both the
-// stores and the group reads below spread over the banks.
-__host__ __device__ inline int degrid_rec_stride(int ts, int P) {
-  const int x = ts * 2 * P;
-  return x + ((8 - x % 32) + 32) % 32;
+// Degridding team reduction buffer. The 2P partial sums of one record are
+// split into groups of QW floats (QW = 4 when P is even, else 2). Thread t of a
+// team stores group q of record r at r*R + q*Q + t*QW: the group stride Q is
+// ts*QW padded to QW (mod 32) floats and the record stride is R = (2P/QW)*Q.
+// A quarter-warp of float4 stores (or a half-warp of float2 stores) then
+// writes consecutive words, and the reducing threads, which read group
+// (r, q) at r*R + q*Q, start in distinct banks. The team stride adds 16 so
+// that two teams in one store phase use opposite halves of the banks.
+__host__ __device__ constexpr int degrid_qw(int P) { return (P % 2 == 0) ? 4 : 2; }
+__host__ __device__ inline int degrid_group_stride(int ts, int P) {
+  const int qw = degrid_qw(P);
+  const int x = ts * qw;
+  return x + ((qw - x % 32) + 32) % 32;
 }
+__host__ __device__ inline int degrid_rec_stride(int ts, int P) { return (2 * P / degrid_qw(P)) * degrid_group_stride(ts, P); }
 __host__ __device__ inline int degrid_team_stride(int ts, int P) { return kRBD * degrid_rec_stride(ts, P) + 16; }
 
 struct SmemLayout {
@@ -367,7 +434,12 @@ __host__ __device__ inline SmemLayout degrid_layout(const Geometry& g, int nthre
 // stepped, not recomputed. There is no per-vector zero test: with B <= 3 no
 // block lies wholly in the padding, and with larger B such a block only adds
 // zeros (one wasted atomic), which is cheaper than testing every vector.
-template <int BU, int BV, int P>
+// Adds a thread's block to the grid with vector atomics. Blocks at the far
+// edge skip their cells outside the grid, which hold exact zeros (the
+// footprint of a gridded visibility is inside the grid). With ZERO the
+// accumulators are cleared afterwards; the chunked loops instead assign the
+// next block.
+template <int BU, int BV, int P, bool ZERO = true>
 __device__ __forceinline__ void flush_global(float2 (&acc)[P][BV][BU], unsigned key, float2* __restrict__ grid, int G) {
   const int u0 = (int)(key & 0xFFFFu) * BU;
   const int v0 = (int)(key >> 16) * BV;
@@ -390,8 +462,10 @@ __device__ __forceinline__ void flush_global(float2 (&acc)[P][BV][BU], unsigned 
         for (int i = 0; i < BU; ++i)
           if (vin && u0 + i < G) atomicAdd(row + i, acc[p][j][i]);
       }
+      if constexpr (ZERO) {
 #pragma unroll
-      for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
+      }
     }
   }
 }
@@ -558,38 +632,110 @@ __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long 
   }
 }
 
-// The thread's block inside the box: position t = (a - rq) mod n per axis,
-// block index q + t (the record stores 4*rq).
-__device__ __forceinline__ unsigned box_key(const int4 m, int au, int av, const Geometry& g, int& tu, int& tv) {
-  const int qu = m.x & 0xFFFF, qv = (int)((unsigned)m.x >> 16);
-  const int rqu = (m.y & 0xFFFF) >> 2, rqv = (int)((unsigned)m.y >> 18);
-  tu = au - rqu;
-  tu += (tu < 0) ? g.nu : 0;
-  tv = av - rqv;
-  tv += (tv < 0) ? g.nv : 0;
-  return (unsigned)(qu + tu) | ((unsigned)(qv + tv) << 16);
-}
+// How a thread forms its Bu x Bv x P products t_u[i] t_v[j] V_p (Sec. 6
+// remark on the separable product). Each product is one packed FMA either way;
+// the forms differ in the multiplies spent beforehand:
+//  - TAP_PRODUCT: Bu*Bv scalar products w_ij = t_u[i] t_v[j];
+//  - TAP_FACTOR_V: Bv*P packed products Y_jp = t_v[j] V_p, then t_u[i] Y_jp;
+//  - TAP_FACTOR_U: Bu*P packed products X_ip = t_u[i] V_p, then t_v[j] X_ip.
+// The cheapest is chosen per instantiation (factoring wins when P < max(Bu, Bv),
+// e.g. for single polarization with Bu or Bv >= 2).
+enum { TAP_PRODUCT = 0, TAP_FACTOR_V = 1, TAP_FACTOR_U = 2 };
+template <int BU, int BV, int P>
+struct TapForm {
+  static constexpr int kProduct = BU * BV, kFactorV = BV * P, kFactorU = BU * P;
+  static constexpr int value = (kProduct <= kFactorV && kProduct <= kFactorU) ? TAP_PRODUCT
+                               : (kFactorV <= kFactorU ? TAP_FACTOR_V : TAP_FACTOR_U);
+};
 
 // The convolution of one visibility into the thread's block (Sec. 3): Bu + Bv
-// taps from the padded tables, Bu*Bv tap products, Bu*Bv*P packed FMAs.
-template <int BU, int BV, int P>
-__device__ __forceinline__ void accumulate(const int4 m, int tu, int tv, const float2* __restrict__ vals,
+// taps from the padded tables, then Bu*Bv*P packed FMAs. With ADD = false the
+// block is assigned instead (acc = products), which starts a fresh block after
+// a flush without zeroing the accumulators first.
+template <int BU, int BV, int P, bool ADD = true>
+__device__ __forceinline__ void accumulate(int offu, int offv, const float2* __restrict__ vals,
                                            const float* __restrict__ tabU, const float* __restrict__ tabV,
                                            float2 (&acc)[P][BV][BU]) {
   float wu[BU], wv[BV];
-  load_taps<BU>(tabU + m.z + tu * BU, wu);
-  load_taps<BV>(tabV + m.w + tv * BV, wv);
+  load_taps<BU>(tabU + offu, wu);
+  load_taps<BV>(tabV + offv, wv);
   float2 V[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) V[p] = vals[p];
+  auto term = [](float2 w, float2 x, float2 c) { return ADD ? __ffma2_rn(w, x, c) : __fmul2_rn(w, x); };
+  constexpr int form = TapForm<BU, BV, P>::value;
+  if constexpr (form == TAP_PRODUCT) {
 #pragma unroll
-  for (int j = 0; j < BV; ++j) {
+    for (int j = 0; j < BV; ++j) {
+#pragma unroll
+      for (int i = 0; i < BU; ++i) {
+        const float2 w2 = splat(wu[i] * wv[j]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) acc[p][j][i] = term(w2, V[p], acc[p][j][i]);
+      }
+    }
+  } else if constexpr (form == TAP_FACTOR_V) {
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float2 Y = __fmul2_rn(splat(wv[j]), V[p]);
+#pragma unroll
+        for (int i = 0; i < BU; ++i) acc[p][j][i] = term(splat(wu[i]), Y, acc[p][j][i]);
+      }
+    }
+  } else {
 #pragma unroll
     for (int i = 0; i < BU; ++i) {
-      const float wgt = wu[i] * wv[j];
-      const float2 w2 = make_float2(wgt, wgt);
 #pragma unroll
-      for (int p = 0; p < P; ++p) acc[p][j][i] = __ffma2_rn(w2, V[p], acc[p][j][i]);
+      for (int p = 0; p < P; ++p) {
+        const float2 X = __fmul2_rn(splat(wu[i]), V[p]);
+#pragma unroll
+        for (int j = 0; j < BV; ++j) acc[p][j][i] = term(splat(wv[j]), X, acc[p][j][i]);
+      }
+    }
+  }
+}
+
+// The adjoint product for degridding: s_p = sum_ij t_u[i] t_v[j] g[p][j][i],
+// in the same three forms (the factored ones sum along one axis first).
+template <int BU, int BV, int P>
+__device__ __forceinline__ void block_dot(const float (&wu)[BU], const float (&wv)[BV], const float2 (&gb)[P][BV][BU],
+                                          float2 (&s)[P]) {
+  constexpr int form = TapForm<BU, BV, P>::value;
+  if constexpr (form == TAP_PRODUCT) {
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+#pragma unroll
+      for (int i = 0; i < BU; ++i) {
+        const float2 w2 = splat(wu[i] * wv[j]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) s[p] = __ffma2_rn(w2, gb[p][j][i], s[p]);
+      }
+    }
+  } else if constexpr (form == TAP_FACTOR_V) {
+    // rows first: r_jp = sum_i t_u[i] g[p][j][i], then s_p += t_v[j] r_jp
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        float2 r = __fmul2_rn(splat(wu[0]), gb[p][j][0]);
+#pragma unroll
+        for (int i = 1; i < BU; ++i) r = __ffma2_rn(splat(wu[i]), gb[p][j][i], r);
+        s[p] = __ffma2_rn(splat(wv[j]), r, s[p]);
+      }
+    }
+  } else {
+    // columns first: c_ip = sum_j t_v[j] g[p][j][i], then s_p += t_u[i] c_ip
+#pragma unroll
+    for (int i = 0; i < BU; ++i) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        float2 c = __fmul2_rn(splat(wv[0]), gb[p][0][i]);
+#pragma unroll
+        for (int j = 1; j < BV; ++j) c = __ffma2_rn(splat(wv[j]), gb[p][j][i], c);
+        s[p] = __ffma2_rn(splat(wu[i]), c, s[p]);
+      }
     }
   }
 }
@@ -630,7 +776,7 @@ __global__ void grid_kernel(Args a) {
 
   const int team = threadIdx.x / g.ts;
   const int l = threadIdx.x - team * g.ts;
-  const int au = l % g.nu, av = l / g.nu;
+  const TeamPos tp = team_pos<BU, BV>(l, g);
   const int nb = (a.chunk_len + kRB - 1) / kRB;
   const unsigned wmask = warp_lane_mask();
   int4* const mt0 = meta + team * kRB;
@@ -662,16 +808,19 @@ __global__ void grid_kernel(Args a) {
       for (int r = 0; r < kRB; ++r) {
         const int4 m = mtb[r];
         if (m.x == (int)kInvalid) continue;
-        int tu, tv;
-        const unsigned key = box_key(m, au, av, g, tu, tv);
+        int offu, offv;
+        const unsigned key = box_key(m, tp, g, offu, offv);
         if (key != cur) {
-          if (cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+          // the box moved: flush the old block and start the new one with this visibility
+          if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
           cur = key;
+          accumulate<BU, BV, P, false>(offu, offv, vlb + r * P, tabU, tabV, acc);
+        } else {
+          accumulate<BU, BV, P>(offu, offv, vlb + r * P, tabU, tabV, acc);
         }
-        accumulate<BU, BV, P>(m, tu, tv, vlb + r * P, tabU, tabV, acc);
       }
     }
-    if (cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+    if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
   } else {
   // ---- patch schedule
   __shared__ int s_item;
@@ -738,13 +887,13 @@ __global__ void grid_kernel(Args a) {
         for (int r = 0; r < kRB; ++r) {
           const int4 m = mtb[r];
           const bool valid = m.x != (int)kInvalid;
-          int tu = 0, tv = 0;
+          int offu = 0, offv = 0;
           unsigned key = cur;
-          if (valid) key = box_key(m, au, av, g, tu, tv);
+          if (valid) key = box_key(m, tp, g, offu, offv);
           window_flush<BU, BV, P>(valid && key != cur && cur != kInvalid, cur, acc, a.grid, g.G, w, dirty);
           if (valid) {
             cur = key;
-            accumulate<BU, BV, P>(m, tu, tv, vlb + r * P, tabU, tabV, acc);
+            accumulate<BU, BV, P>(offu, offv, vlb + r * P, tabU, tabV, acc);
           }
         }
       }
@@ -836,13 +985,15 @@ __global__ void degrid_kernel(Args a) {
 
   const int team = threadIdx.x / g.ts;
   const int l = threadIdx.x - team * g.ts;
-  const int au = l % g.nu, av = l / g.nu;
+  const TeamPos tp = team_pos<BU, BV>(l, g);
   const unsigned wmask = warp_lane_mask();
   const long long chunk = (long long)blockIdx.x * g.tpc + team;
   const long long vbeg = chunk * a.chunk_len;
   const long long vend = chunk < a.n_chunks ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
   int4* const mt0 = meta + team * kRBD;
   int4* const mt1 = meta + (g.tpc + team) * kRBD;
+  constexpr int QW = degrid_qw(P);
+  const int Q = degrid_group_stride(g.ts, P);
   const int R = degrid_rec_stride(g.ts, P);
   float* red = (float*)(smem + L.red) + (size_t)team * degrid_team_stride(g.ts, P);
   const int nb = (a.chunk_len + kRBD - 1) / kRBD;
@@ -867,55 +1018,44 @@ __global__ void degrid_kernel(Args a) {
 #pragma unroll
       for (int p = 0; p < P; ++p) s[p] = make_float2(0.f, 0.f);
       if (m.x != (int)kInvalid) {
-        int tu, tv;
-        const unsigned key = box_key(m, au, av, g, tu, tv);
+        int offu, offv;
+        const unsigned key = box_key(m, tp, g, offu, offv);
         if (key != cur) {
           load_block<BU, BV, P>(gb, key, a.grid, g.G);
           cur = key;
         }
         float wu[BU], wv[BV];
-        load_taps<BU>(tabU + m.z + tu * BU, wu);
-        load_taps<BV>(tabV + m.w + tv * BV, wv);
-#pragma unroll
-        for (int j = 0; j < BV; ++j) {
-#pragma unroll
-          for (int i = 0; i < BU; ++i) {
-            const float wgt = wu[i] * wv[j];
-            const float2 w2 = make_float2(wgt, wgt);
-#pragma unroll
-            for (int p = 0; p < P; ++p) s[p] = __ffma2_rn(w2, gb[p][j][i], s[p]);
-          }
-        }
+        load_taps<BU>(tabU + offu, wu);
+        load_taps<BV>(tabV + offv, wv);
+        block_dot<BU, BV, P>(wu, wv, gb, s);
       }
-      float* dst = red + r * R + l * 2 * P;
-      if constexpr (P % 2 == 0) {
+      float* dst = red + r * R + l * QW;
+      if constexpr (QW == 4) {
 #pragma unroll
-        for (int p = 0; p < P; p += 2) *(float4*)(dst + 2 * p) = make_float4(s[p].x, s[p].y, s[p + 1].x, s[p + 1].y);
+        for (int p = 0; p < P; p += 2) *(float4*)(dst + (p / 2) * Q) = make_float4(s[p].x, s[p].y, s[p + 1].x, s[p + 1].y);
       } else {
 #pragma unroll
-        for (int p = 0; p < P; ++p) *(float2*)(dst + 2 * p) = s[p];
+        for (int p = 0; p < P; ++p) *(float2*)(dst + p * Q) = s[p];
       }
     }
     group_sync(a, wmask);
-    // Each team thread reduces whole groups of components over the team:
-    // 4 components (2 complex values) per group when P >= 2, else 2.
+    // Each team thread reduces whole groups of QW components over the team.
     {
-      constexpr int QW = (P % 2 == 0) ? 4 : 2;
       constexpr int GPR = 2 * P / QW;
       for (int gi = l; gi < kRBD * GPR; gi += g.ts) {
         const int r = gi / GPR;
         const int q = gi - r * GPR;
         const long long k = vbeg + (long long)b * kRBD + r;
         if (k >= vend) continue;
-        const float* col = red + r * R + q * QW;
+        const float* col = red + r * R + q * Q;
         float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
         for (int t = 0; t < g.ts; ++t) {
           if constexpr (QW == 4) {
-            const float4 v4 = *(const float4*)(col + t * 2 * P);
+            const float4 v4 = *(const float4*)(col + t * QW);
             s0 = __fadd2_rn(s0, make_float2(v4.x, v4.y));
             s1 = __fadd2_rn(s1, make_float2(v4.z, v4.w));
           } else {
-            s0 = __fadd2_rn(s0, *(const float2*)(col + t * 2 * P));
+            s0 = __fadd2_rn(s0, *(const float2*)(col + t * QW));
           }
         }
         if (a.weights) {
@@ -1027,11 +1167,7 @@ __global__ void grid_batch_kernel(BatchArgs b) {
     const BatchItem it = b.items[u.x];
     Args a;
     a.g.G = b.G; a.g.S = it.S; a.g.O = b.O; a.g.log2O = b.log2O; a.g.h = (it.S - 1) / 2; a.g.P = P;
-    a.g.nbu = ((it.S + BU - 1 + BU - 1) / BU) * BU;
-    a.g.nbv = ((it.S + BV - 1 + BV - 1) / BV) * BV;
-    a.g.nu = a.g.nbu / BU;
-    a.g.nv = a.g.nbv / BV;
-    a.g.ts = a.g.nu * a.g.nv;
+    finish_geometry(a.g, BU, BV);
     a.g.tpc = min(b.tpc_max, (int)blockDim.x / a.g.ts);
     a.n_vis = it.n_vis;
     a.uv = it.uv;
@@ -1055,7 +1191,7 @@ __global__ void grid_batch_kernel(BatchArgs b) {
     const int team = threadIdx.x / g.ts;
     const int l = threadIdx.x - team * g.ts;
     const bool active = team < u.z;  // u.z <= tpc chunks in this unit
-    const int au = l % g.nu, av = l / g.nu;
+    const TeamPos tp = team_pos<BU, BV>(l, g);
       const long long chunk = (long long)u.y + team;
     const long long vbeg = chunk * b.chunk_len;
     const long long vend = active ? min(vbeg + b.chunk_len, it.n_vis) : vbeg;
@@ -1081,17 +1217,19 @@ __global__ void grid_batch_kernel(BatchArgs b) {
         for (int r = 0; r < kRB; ++r) {
           const int4 m = mtb[r];
           if (m.x == (int)kInvalid) continue;
-          int tu, tv;
-          const unsigned key = box_key(m, au, av, g, tu, tv);
+          int offu, offv;
+          const unsigned key = box_key(m, tp, g, offu, offv);
           if (key != cur) {
-            if (cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+            if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
             cur = key;
+            accumulate<BU, BV, P, false>(offu, offv, vlb + r * P, tabU, tabV, acc);
+          } else {
+            accumulate<BU, BV, P>(offu, offv, vlb + r * P, tabU, tabV, acc);
           }
-          accumulate<BU, BV, P>(m, tu, tv, vlb + r * P, tabU, tabV, acc);
         }
       }
     }
-    if (active && cur != kInvalid) flush_global<BU, BV, P>(acc, cur, a.grid, g.G);
+    if (active && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
   }
 }
 

@@ -133,11 +133,7 @@ int grid_patch_static(int G, int S, int oversample, int npol, int Bu, int Bv, in
   memset(&g, 0, sizeof g);
   g.G = G; g.S = S; g.O = oversample; g.h = (S - 1) / 2; g.P = npol;
   while ((1 << g.log2O) < oversample) ++g.log2O;
-  g.nbu = ((S + Bu - 1 + Bu - 1) / Bu) * Bu;
-  g.nbv = ((S + Bv - 1 + Bv - 1) / Bv) * Bv;
-  g.nu = g.nbu / Bu;
-  g.nv = g.nbv / Bv;
-  g.ts = g.nu * g.nv;
+  finish_geometry(g, Bu, Bv);
   cudaFuncAttributes fa;
   e = cudaFuncGetAttributes(&fa, k->grid_patch_fn);
   if (e != cudaSuccess) return sfail(GRID_ERR_CUDA, cudaGetErrorString(e));
