@@ -20,6 +20,7 @@ Usage:
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="auto", help="grid plan: auto | chunked:Bu,Bv[:vis_per_chunk] | patch:Bu,Bv[:vis_per_chunk]")
+    ap.add_argument("--config", default="auto", help="grid plan: auto | chunked:Bu,Bv[:vis_per_chunk[:threads]] | patch:Bu,Bv[:vis_per_chunk[:threads]]")
     ap.add_argument("--degrid-config", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -258,12 +259,14 @@ def measure_compression(gb, autotune, torch, dev, cfg_grid, cfg_degrid, steps, w
 
 
 def parse_cfg(s):
-    """'chunked:Bu,Bv' or 'chunked:Bu,Bv:L' (L visibilities per chunk) -> plan config dict."""
+    """'chunked:Bu,Bv[:L[:T]]' (L visibilities per chunk, T threads per CTA) -> plan config dict."""
     parts = s.split(":")
     bu, bv = (int(x) for x in parts[1].split(","))
     cfg = dict(schedule=parts[0], Bu=bu, Bv=bv)
     if len(parts) > 2:
         cfg["vis_per_chunk"] = int(parts[2])
+    if len(parts) > 3:
+        cfg["threads"] = int(parts[3])
     return cfg
 
 
@@ -366,11 +369,16 @@ def main():
     dominant = "grid" if g_ms >= d_ms else "degrid"
     achieved = g_tflops if dominant == "grid" else d_tflops
 
+    # DRAM bytes per launch from one ncu capture (profiles/traffic.json), used only while the
+    # kernel source is the one that was captured
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
+    if os.path.exists(tpath) and not args.vis:
         try:
-            traffic = json.load(open(tpath)).get(dominant)
+            rec = json.load(open(tpath))
+            src = open(os.path.join(ROOT, "paper_1605_07023_gb300", "csrc", "kernels.cuh"), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == rec.get("kernels_cuh_sha256_16"):
+                traffic = rec.get(dominant)
         except Exception:
             traffic = None
 

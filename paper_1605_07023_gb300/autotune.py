@@ -22,6 +22,10 @@ from . import synth
 BLOCK_CANDIDATES = [(1, 1), (2, 1), (1, 2), (2, 2), (4, 2), (2, 4), (3, 3), (4, 4), (8, 2), (2, 8)]
 CHUNKED_LENGTHS = (128, 256, 1024)
 PATCH_LENGTHS = (32, 64)
+DEGRID_LENGTHS = (64, 128, 256)
+# Target CTA sizes (threads per CTA, rounded down to whole teams). Smaller CTAs let more of the
+# register-limited teams be resident per SM.
+CTA_THREADS = (128, 256)
 
 
 def _cache_path() -> str:
@@ -64,12 +68,14 @@ def _candidates(kind: str):
     for bu, bv in BLOCK_CANDIDATES:
         if kind == "grid":
             for L in CHUNKED_LENGTHS:
-                yield dict(schedule="chunked", Bu=bu, Bv=bv, vis_per_chunk=L)
+                for T in CTA_THREADS:
+                    yield dict(schedule="chunked", Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
             for L in PATCH_LENGTHS:
                 yield dict(schedule="patch", Bu=bu, Bv=bv, vis_per_chunk=L)
         else:
-            for L in (64, 256, 1024):
-                yield dict(schedule="chunked", Bu=bu, Bv=bv, vis_per_chunk=L)
+            for L in DEGRID_LENGTHS:
+                for T in CTA_THREADS:
+                    yield dict(schedule="chunked", Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
 
 
 def _time(fn, reps: int) -> float:
