@@ -123,18 +123,12 @@ __device__ __forceinline__ bool fine_cell(double x, int log2O, int halfG, int& C
   return true;
 }
 
-// L2 cache policies. The inputs (uv, visibilities, weights) are read once and
-// stream through L2 (evict first, no L1 allocation). The grid is updated or
-// read many times and should stay resident in L2 (evict last): it is about
-// the size of GB300's L2, and the streaming inputs would otherwise push it out.
+// L2 cache policies. The degridder's inputs (uv) and outputs stream through
+// L2 (evict first, no L1 allocation). Grid reads use plain non-coherent
+// loads: an evict-last hint on them was measured 8-11% slower.
 __device__ __forceinline__ unsigned long long policy_stream() {
   unsigned long long p;
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ unsigned long long policy_keep() {
-  unsigned long long p;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ double2 ld_stream(const double2* p) {
@@ -176,28 +170,6 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy_stream()));
   return v;
-}
-// grid reads (degridding): keep the lines in L2
-__device__ __forceinline__ float4 ld_keep(const float4* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(policy_keep()));
-  return v;
-}
-__device__ __forceinline__ float2 ld_keep(const float2* p) {
-  float2 v;
-  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(policy_keep()));
-  return v;
-}
-// grid atomics: vector reductions that keep the grid's lines in L2
-__device__ __forceinline__ void red_keep(float4* p, float4 v) {
-  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w), "l"(policy_keep())
-               : "memory");
-}
-__device__ __forceinline__ void red_keep(float2* p, float2 v) {
-  asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(policy_keep())
-               : "memory");
 }
 // output visibilities (degridding): written once
 __device__ __forceinline__ void st_stream(float* p, float v) {
@@ -439,34 +411,63 @@ __host__ __device__ inline SmemLayout degrid_layout(const Geometry& g, int nthre
 // footprint of a gridded visibility is inside the grid). With ZERO the
 // accumulators are cleared afterwards; the chunked loops instead assign the
 // next block.
+// Adds a thread's block to the grid with vector atomics. Cells are addressed
+// by a 32-bit index from the grid base (P*G*G <= 2^32 for G <= 32768), so a
+// cell address is one add and one wide multiply-add. A block wholly inside
+// the grid takes the unguarded path; blocks at the far edge skip their cells
+// outside the grid, which hold exact zeros (the footprint of a gridded
+// visibility is inside the grid). With ZERO the accumulators are cleared
+// afterwards; the chunked loops instead assign the next block.
 template <int BU, int BV, int P, bool ZERO = true>
 __device__ __forceinline__ void flush_global(float2 (&acc)[P][BV][BU], unsigned key, float2* __restrict__ grid, int G) {
-  const int u0 = (int)(key & 0xFFFFu) * BU;
-  const int v0 = (int)(key >> 16) * BV;
-  const size_t plane = (size_t)G * G;
-  float2* base = grid + (size_t)v0 * G + u0;
+  const unsigned u0 = (key & 0xFFFFu) * BU;
+  const unsigned v0 = (key >> 16) * BV;
+  const unsigned GG = (unsigned)G * (unsigned)G;
+  const unsigned base = v0 * (unsigned)G + u0;
+  if (u0 + BU <= (unsigned)G && v0 + BV <= (unsigned)G) {
 #pragma unroll
-  for (int j = 0; j < BV; ++j) {
-    const bool vin = v0 + j < G;
+    for (int j = 0; j < BV; ++j)
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      float2* row = base + p * plane + (size_t)j * G;
-      if constexpr (BU % 2 == 0) {
+      for (int p = 0; p < P; ++p) {
+        const unsigned row = base + (unsigned)p * GG + (unsigned)j * (unsigned)G;
+        if constexpr (BU % 2 == 0) {
 #pragma unroll
-        for (int i = 0; i < BU; i += 2) {
-          if (vin && u0 + i + 1 < G)
-            atomicAdd((float4*)(row + i), make_float4(acc[p][j][i].x, acc[p][j][i].y, acc[p][j][i + 1].x, acc[p][j][i + 1].y));
+          for (int i = 0; i < BU; i += 2)
+            atomicAdd((float4*)(grid + (row + i)),
+                      make_float4(acc[p][j][i].x, acc[p][j][i].y, acc[p][j][i + 1].x, acc[p][j][i + 1].y));
+        } else {
+#pragma unroll
+          for (int i = 0; i < BU; ++i) atomicAdd(grid + (row + i), acc[p][j][i]);
         }
-      } else {
-#pragma unroll
-        for (int i = 0; i < BU; ++i)
-          if (vin && u0 + i < G) atomicAdd(row + i, acc[p][j][i]);
       }
-      if constexpr (ZERO) {
+  } else {
 #pragma unroll
-        for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
+    for (int j = 0; j < BV; ++j) {
+      if (v0 + j >= (unsigned)G) continue;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const unsigned row = base + (unsigned)p * GG + (unsigned)j * (unsigned)G;
+        if constexpr (BU % 2 == 0) {
+#pragma unroll
+          for (int i = 0; i < BU; i += 2)
+            if (u0 + i + 1 < (unsigned)G)
+              atomicAdd((float4*)(grid + (row + i)),
+                        make_float4(acc[p][j][i].x, acc[p][j][i].y, acc[p][j][i + 1].x, acc[p][j][i + 1].y));
+        } else {
+#pragma unroll
+          for (int i = 0; i < BU; ++i)
+            if (u0 + i < (unsigned)G) atomicAdd(grid + (row + i), acc[p][j][i]);
+        }
       }
     }
+  }
+  if constexpr (ZERO) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 0; j < BV; ++j)
+#pragma unroll
+        for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
   }
 }
 
@@ -925,7 +926,7 @@ __global__ void grid_kernel(Args a) {
         if (nz) {
           const int gu = w.wu0 + lu, gv = w.wv0 + vv;
           if (gu >= 0 && gv >= 0 && gu + 1 < g.G && gv < g.G)
-            red_keep((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
+            atomicAdd((float4*)(a.grid + ((size_t)p * g.G + gv) * g.G + gu), q);
           *src = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
@@ -943,19 +944,22 @@ __global__ void grid_kernel(Args a) {
 // outputs.
 template <int BU, int BV, int P>
 __device__ __forceinline__ void load_block(float2 (&gb)[P][BV][BU], unsigned key, const float2* __restrict__ grid, int G) {
-  const int u0 = (int)(key & 0xFFFFu) * BU;
-  const int v0 = (int)(key >> 16) * BV;
+  const unsigned u0 = (key & 0xFFFFu) * BU;
+  const unsigned v0 = (key >> 16) * BV;
+  const unsigned GG = (unsigned)G * (unsigned)G;
+  const unsigned base = v0 * (unsigned)G + u0;
+  const bool inside = u0 + BU <= (unsigned)G && v0 + BV <= (unsigned)G;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
 #pragma unroll
     for (int j = 0; j < BV; ++j) {
-      const int v = v0 + j;
-      const float2* row = grid + ((size_t)p * G + v) * G + u0;
+      const unsigned row = base + (unsigned)p * GG + (unsigned)j * (unsigned)G;
+      const bool vin = inside || v0 + j < (unsigned)G;
       if constexpr (BU % 2 == 0) {
 #pragma unroll
         for (int i = 0; i < BU; i += 2) {
           float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (v < G && u0 + i + 1 < G) q = ld_keep((const float4*)(row + i));
+          if (inside || (vin && u0 + i + 1 < (unsigned)G)) q = __ldg((const float4*)(grid + (row + i)));
           gb[p][j][i] = make_float2(q.x, q.y);
           gb[p][j][i + 1] = make_float2(q.z, q.w);
         }
@@ -963,7 +967,7 @@ __device__ __forceinline__ void load_block(float2 (&gb)[P][BV][BU], unsigned key
 #pragma unroll
         for (int i = 0; i < BU; ++i) {
           float2 q = make_float2(0.f, 0.f);
-          if (v < G && u0 + i < G) q = ld_keep(row + i);
+          if (inside || (vin && u0 + i < (unsigned)G)) q = __ldg(grid + (row + i));
           gb[p][j][i] = q;
         }
       }
