@@ -225,6 +225,14 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     s.win = win;
     s.max_chunks = 256;
   }
+  if (d.schedule == GRID_SCHED_CHUNKED) {
+    // small teams (tiny S and B) put many teams in a CTA: shrink the CTA until
+    // its staging buffers fit
+    while (g.tpc > 1 && (k->grid_smem(g, g.tpc * g.ts, 0) + fa_g.sharedSizeBytes > smem_max ||
+                         k->degrid_smem(g, g.tpc * g.ts, 0) + fa_d.sharedSizeBytes > smem_max))
+      --g.tpc;
+    pl->threads = g.tpc * g.ts;
+  }
   pl->smem_grid = k->grid_smem(g, pl->threads, win);
   pl->smem_degrid = k->degrid_smem(g, pl->threads, 0);
   if (pl->smem_grid + fa_g.sharedSizeBytes > smem_max || pl->smem_degrid + fa_d.sharedSizeBytes > smem_max) {

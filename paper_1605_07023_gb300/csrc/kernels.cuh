@@ -35,7 +35,7 @@
 namespace gbg {
 
 constexpr unsigned kInvalid = 0xFFFFFFFFu;
-constexpr int kRB = 16;   // records per team per staged batch (gridding)
+constexpr int kRB = 32;   // records per team per staged batch (gridding)
 constexpr int kRBD = 8;   // records per team per batch (degridding; bounded by the reduction buffer)
 constexpr int kSlots = 8; // flush slots per warp (lanes parked per cooperative-flush round)
 
@@ -649,53 +649,77 @@ struct TapForm {
                                : (kFactorV <= kFactorU ? TAP_FACTOR_V : TAP_FACTOR_U);
 };
 
-// The convolution of one visibility into the thread's block (Sec. 3): Bu + Bv
-// taps from the padded tables, then Bu*Bv*P packed FMAs. With ADD = false the
-// block is assigned instead (acc = products), which starts a fresh block after
-// a flush without zeroing the accumulators first.
+// The convolution of one visibility into the thread's block (Sec. 3), in two
+// steps so that the part common to every lane is done before the branch on
+// whether the block changed:
+//  - Contribution::prepare: Bu + Bv taps from the padded tables, the values,
+//    and the products the chosen form needs;
+//  - Contribution::apply: Bu*Bv*P packed FMAs into the accumulators, or (ADD =
+//    false) packed multiplies that assign a fresh block after a flush.
+template <int BU, int BV, int P>
+struct Contribution {
+  static constexpr int form = TapForm<BU, BV, P>::value;
+  static constexpr int NA = form == TAP_PRODUCT ? BV * BU : (form == TAP_FACTOR_V ? BV * P : BU * P);
+  static constexpr int NB = form == TAP_PRODUCT ? 1 : (form == TAP_FACTOR_V ? BU : BV);
+  // PRODUCT: A = tap products t_u t_v (scalars), V = values.
+  // FACTOR_V: A = t_v V (pairs), t = t_u.  FACTOR_U: A = t_u V (pairs), t = t_v.
+  float a[form == TAP_PRODUCT ? NA : 1];
+  float2 A[form == TAP_PRODUCT ? 1 : NA];
+  float2 V[form == TAP_PRODUCT ? P : 1];
+  float t[NB];
+
+  __device__ __forceinline__ void prepare(int offu, int offv, const float2* __restrict__ vals,
+                                          const float* __restrict__ tabU, const float* __restrict__ tabV) {
+    float wu[BU], wv[BV];
+    load_taps<BU>(tabU + offu, wu);
+    load_taps<BV>(tabV + offv, wv);
+    if constexpr (form == TAP_PRODUCT) {
+#pragma unroll
+      for (int j = 0; j < BV; ++j)
+#pragma unroll
+        for (int i = 0; i < BU; ++i) a[j * BU + i] = wu[i] * wv[j];
+#pragma unroll
+      for (int p = 0; p < P; ++p) V[p] = vals[p];
+    } else if constexpr (form == TAP_FACTOR_V) {
+#pragma unroll
+      for (int j = 0; j < BV; ++j)
+#pragma unroll
+        for (int p = 0; p < P; ++p) A[j * P + p] = __fmul2_rn(splat(wv[j]), vals[p]);
+#pragma unroll
+      for (int i = 0; i < BU; ++i) t[i] = wu[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < BU; ++i)
+#pragma unroll
+        for (int p = 0; p < P; ++p) A[i * P + p] = __fmul2_rn(splat(wu[i]), vals[p]);
+#pragma unroll
+      for (int j = 0; j < BV; ++j) t[j] = wv[j];
+    }
+  }
+
+  template <bool ADD>
+  __device__ __forceinline__ void apply(float2 (&acc)[P][BV][BU]) const {
+    auto term = [](float2 x, float2 y, float2 c) { return ADD ? __ffma2_rn(x, y, c) : __fmul2_rn(x, y); };
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 0; j < BV; ++j)
+#pragma unroll
+        for (int i = 0; i < BU; ++i) {
+          if constexpr (form == TAP_PRODUCT) acc[p][j][i] = term(splat(a[j * BU + i]), V[p], acc[p][j][i]);
+          else if constexpr (form == TAP_FACTOR_V) acc[p][j][i] = term(splat(t[i]), A[j * P + p], acc[p][j][i]);
+          else acc[p][j][i] = term(splat(t[j]), A[i * P + p], acc[p][j][i]);
+        }
+  }
+};
+
 template <int BU, int BV, int P, bool ADD = true>
 __device__ __forceinline__ void accumulate(int offu, int offv, const float2* __restrict__ vals,
                                            const float* __restrict__ tabU, const float* __restrict__ tabV,
                                            float2 (&acc)[P][BV][BU]) {
-  float wu[BU], wv[BV];
-  load_taps<BU>(tabU + offu, wu);
-  load_taps<BV>(tabV + offv, wv);
-  float2 V[P];
-#pragma unroll
-  for (int p = 0; p < P; ++p) V[p] = vals[p];
-  auto term = [](float2 w, float2 x, float2 c) { return ADD ? __ffma2_rn(w, x, c) : __fmul2_rn(w, x); };
-  constexpr int form = TapForm<BU, BV, P>::value;
-  if constexpr (form == TAP_PRODUCT) {
-#pragma unroll
-    for (int j = 0; j < BV; ++j) {
-#pragma unroll
-      for (int i = 0; i < BU; ++i) {
-        const float2 w2 = splat(wu[i] * wv[j]);
-#pragma unroll
-        for (int p = 0; p < P; ++p) acc[p][j][i] = term(w2, V[p], acc[p][j][i]);
-      }
-    }
-  } else if constexpr (form == TAP_FACTOR_V) {
-#pragma unroll
-    for (int j = 0; j < BV; ++j) {
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float2 Y = __fmul2_rn(splat(wv[j]), V[p]);
-#pragma unroll
-        for (int i = 0; i < BU; ++i) acc[p][j][i] = term(splat(wu[i]), Y, acc[p][j][i]);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < BU; ++i) {
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const float2 X = __fmul2_rn(splat(wu[i]), V[p]);
-#pragma unroll
-        for (int j = 0; j < BV; ++j) acc[p][j][i] = term(splat(wv[j]), X, acc[p][j][i]);
-      }
-    }
-  }
+  Contribution<BU, BV, P> c;
+  c.prepare(offu, offv, vals, tabU, tabV);
+  c.template apply<ADD>(acc);
 }
 
 // The adjoint product for degridding: s_p = sum_ij t_u[i] t_v[j] g[p][j][i],
@@ -811,13 +835,17 @@ __global__ void grid_kernel(Args a) {
         if (m.x == (int)kInvalid) continue;
         int offu, offv;
         const unsigned key = box_key(m, tp, g, offu, offv);
-        if (key != cur) {
-          // the box moved: flush the old block and start the new one with this visibility
-          if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+        // the box moved: flush the old block, then start the new one with this
+        // visibility (the contribution is prepared by all lanes between the two)
+        const bool moved = key != cur;
+        if (moved && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+        Contribution<BU, BV, P> c;
+        c.prepare(offu, offv, vlb + r * P, tabU, tabV);
+        if (moved) {
           cur = key;
-          accumulate<BU, BV, P, false>(offu, offv, vlb + r * P, tabU, tabV, acc);
+          c.template apply<false>(acc);
         } else {
-          accumulate<BU, BV, P>(offu, offv, vlb + r * P, tabU, tabV, acc);
+          c.template apply<true>(acc);
         }
       }
     }
@@ -1223,12 +1251,17 @@ __global__ void grid_batch_kernel(BatchArgs b) {
           if (m.x == (int)kInvalid) continue;
           int offu, offv;
           const unsigned key = box_key(m, tp, g, offu, offv);
-          if (key != cur) {
-            if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+          // the box moved: flush the old block, then start the new one with this
+          // visibility (the contribution is prepared by all lanes between the two)
+          const bool moved = key != cur;
+          if (moved && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+          Contribution<BU, BV, P> c;
+          c.prepare(offu, offv, vlb + r * P, tabU, tabV);
+          if (moved) {
             cur = key;
-            accumulate<BU, BV, P, false>(offu, offv, vlb + r * P, tabU, tabV, acc);
+            c.template apply<false>(acc);
           } else {
-            accumulate<BU, BV, P>(offu, offv, vlb + r * P, tabU, tabV, acc);
+            c.template apply<true>(acc);
           }
         }
       }
