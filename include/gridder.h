@@ -194,6 +194,34 @@ int grid_compress(grid_plan_t plan, int64_t n_vis, const double* uv, const void*
                   double* uv_out, void* vis_out, int64_t* run_of, int64_t* n_out, cudaStream_t stream);
 
 /*
+ * One gridding and degridding pass from HOST buffers, with the transfers
+ * overlapped with the kernels (a pipeline over chunks of `chunk`
+ * visibilities; 0 = 1,048,576):
+ *   - the grid is zeroed, chunk c of uv, values and weights is uploaded on a
+ *     copy stream while chunk c-1 is gridded on `stream`;
+ *   - the grid is copied down (if grid_host is not NULL) while the
+ *     visibilities are degridded, and each degridded chunk is copied down
+ *     while the next one is degridded.
+ * gplan grids and dplan degrids; they must agree in G, S, oversample, npol
+ * and precision (they may be the same plan).
+ * HOST buffers (pinned, for the copies to overlap): uv_host [n][2] f64,
+ * vis_host [n][npol] in the plan precision, weights_host [n] f32 or NULL,
+ * vis_out_host [n][npol] complex64 (the degridded values, unweighted),
+ * grid_host [npol][G][G] complex64 or NULL.
+ * DEVICE buffers (caller-owned, room for n visibilities, aligned as for
+ * grid()): uv_dev, vis_dev, weights_dev (needed when weights_host is given),
+ * vis_out_dev, kernel_table, grid_dev (overwritten: zeroed, then gridded).
+ * The work is ordered after earlier work on `stream`, and later work on
+ * `stream` sees every output; the host outputs are complete once `stream`
+ * reaches that point. The plan keeps a copy stream and events (created on
+ * first use). Returns GRID_OK or a negative error code.
+ */
+int grid_degrid_host(grid_plan_t gplan, grid_plan_t dplan, int64_t n_vis, const double* uv_host, const void* vis_host,
+                     const float* weights_host, double* uv_dev, void* vis_dev, float* weights_dev, void* vis_out_dev,
+                     const void* kernel_table, void* grid_dev, void* vis_out_host, void* grid_host, int64_t chunk,
+                     cudaStream_t stream);
+
+/*
  * Expansion after degridding compressed records: every member of a run has
  * the run's fine position, so its degridded value is the run's.
  *   vis_out[k][p] = w_k * vis_compressed[run_of[k]][p]   (w_k = 1 if weights is NULL)

@@ -217,6 +217,50 @@ def degrid_expand(plan: Plan, run_of, vis_c, weights=None, vis_out=None, stream=
     return vis_out
 
 
+def _hptr(t, name: str, dtype=None) -> int:
+    torch = _torch()
+    if t is None:
+        return 0
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    return t.data_ptr()
+
+
+def grid_degrid_host(gplan: Plan, dplan: Plan, uv_host, vis_host, weights_host, kernel_table, grid, vis_out_host,
+                     grid_host=None, work=None, chunk: int = 0, stream=None):
+    """grid_degrid_host(): zero the grid, grid and degrid from HOST (pinned) buffers with the copies overlapped.
+
+    ``work`` = (uv_dev, vis_dev, weights_dev, vis_out_dev) device buffers with room for n visibilities
+    (allocated here if None). Fills vis_out_host (and grid_host if given) once the stream reaches the end
+    of the call. Returns vis_out_host.
+    """
+    torch = _torch()
+    n = uv_host.shape[0]
+    dev = grid.device
+    if work is None:
+        work = (torch.empty((n, 2), dtype=torch.float64, device=dev), torch.empty_like(vis_host, device=dev),
+                None if weights_host is None else torch.empty_like(weights_host, device=dev),
+                torch.empty((n, gplan.npol), dtype=torch.complex64, device=dev))
+    uv_d, vis_d, wt_d, out_d = work
+    if vis_host.shape[0] != n or (weights_host is not None and weights_host.shape[0] != n) or vis_out_host.shape[0] != n:
+        raise ValueError("host buffers must have one row per visibility")
+    if tuple(grid.shape) != (gplan.npol, gplan.G, gplan.G):
+        raise ValueError(f"grid must be [{gplan.npol}, {gplan.G}, {gplan.G}]")
+    args = (gplan.handle, dplan.handle, n, _hptr(uv_host, "uv_host", torch.float64),
+            _hptr(vis_host, "vis_host", _vis_dtype(gplan)), _hptr(weights_host, "weights_host", torch.float32) or None,
+            _dptr(uv_d, "uv_dev", torch.float64, 2), _dptr(vis_d, "vis_dev", _vis_dtype(gplan)),
+            _dptr(wt_d, "weights_dev", torch.float32, 1) or None, _dptr(out_d, "vis_out_dev", torch.complex64, 2),
+            _dptr(kernel_table, "kernel_table", (torch.float32, torch.bfloat16, torch.float16), 2),
+            _dptr(grid, "grid", torch.complex64, 3), _hptr(vis_out_host, "vis_out_host", torch.complex64),
+            _hptr(grid_host, "grid_host", torch.complex64) or None, int(chunk), _stream_ptr(stream))
+    _lib.check(_lib.load().grid_degrid_host(*args))
+    return vis_out_host
+
+
 def grid_make_kernel_table(S: int, oversample: int, beta: float, precision: str = "f32", device=None, stream=None):
     """Oversampled Kaiser-Bessel table [O, S], computed on the device in FP64 and rounded once."""
     torch = _torch()

@@ -24,7 +24,7 @@ EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "gr
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
            "grid_last_error", "grid_device_info", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
            "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
-           "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand")
+           "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host")
 
 
 class GridBatchItem(ctypes.Structure):
@@ -85,6 +85,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid_compress.restype = i32
     lib.degrid_expand.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp]
     lib.degrid_expand.restype = i32
+    lib.grid_degrid_host.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
+    lib.grid_degrid_host.restype = i32
     lib.grid_last_error.argtypes = []
     lib.grid_last_error.restype = ctypes.c_char_p
     lib.grid_device_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]

@@ -1,5 +1,6 @@
 // C ABI of the GB300 gridder: plan management, validation and kernel launch.
 // The declarations and their contracts are in include/gridder.h.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +29,9 @@ struct grid_plan_s {
   long long ps_chunks_cap;  // chunk capacity of the patch scratch
   void* cs_buf;             // compression scratch (grow-only)
   size_t cs_bytes;
+  cudaStream_t cstream;     // copy stream of grid_degrid_host (created on first use)
+  cudaEvent_t* evs;         // its events (grow-only)
+  int n_evs;
 };
 
 namespace {
@@ -263,6 +267,9 @@ void grid_plan_destroy(grid_plan_t pl) {
   if (!pl) return;
   free_patch(pl);
   cudaFree(pl->cs_buf);
+  for (int i = 0; i < pl->n_evs; ++i) cudaEventDestroy(pl->evs[i]);
+  delete[] pl->evs;
+  if (pl->cstream) cudaStreamDestroy(pl->cstream);
   cudaFree(pl->d_skipped);
   delete pl;
 }
@@ -449,6 +456,92 @@ int degrid_expand(grid_plan_t pl, int64_t n_vis, const int64_t* run_of, int64_t 
   cudaError_t e = launch_expand(pl->g.P, n_vis, (const long long*)run_of, n_compressed, (const float2*)vis_compressed,
                                 weights, (float2*)vis_out, pl->sm_count, stream);
   if (e != cudaSuccess) return cuda_fail(e, "expand kernel launch");
+  return GRID_OK;
+}
+
+int grid_degrid_host(grid_plan_t gp, grid_plan_t dp, int64_t n_vis, const double* uv_host, const void* vis_host,
+                     const float* weights_host, double* uv_dev, void* vis_dev, float* weights_dev, void* vis_out_dev,
+                     const void* kernel_table, void* grid_dev, void* vis_out_host, void* grid_host, int64_t chunk,
+                     cudaStream_t stream) {
+  g_err.clear();
+  if (!gp || !dp) return fail(GRID_ERR_INVALID, "null plan");
+  const Geometry &a = gp->g, &b = dp->g;
+  if (a.G != b.G || a.S != b.S || a.O != b.O || a.P != b.P || gp->desc.precision != dp->desc.precision)
+    return fail(GRID_ERR_INVALID, "the two plans differ in G, S, oversample, npol or precision");
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
+  if (!kernel_table || !grid_dev) return fail(GRID_ERR_INVALID, "null kernel_table or grid");
+  if (n_vis > 0 && (!uv_host || !vis_host || !uv_dev || !vis_dev || !vis_out_dev || !vis_out_host))
+    return fail(GRID_ERR_INVALID, "null uv, vis or vis_out buffer");
+  if (weights_host && !weights_dev) return fail(GRID_ERR_INVALID, "weights_host needs weights_dev");
+  if (chunk < 0) return fail(GRID_ERR_INVALID, "chunk=%lld", (long long)chunk);
+  int rc = check_device(gp);
+  if (rc) return rc;
+  if (chunk == 0) chunk = 1 << 20;
+  const long long nc = n_vis > 0 ? (n_vis + chunk - 1) / chunk : 0;
+  if (nc > 4096) return fail(GRID_ERR_INVALID, "%lld chunks: use a larger chunk", nc);
+  const int need_ev = (int)(2 * nc + 3);
+  cudaError_t e = cudaSuccess;
+  if (!gp->cstream) e = cudaStreamCreateWithFlags(&gp->cstream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+  if (gp->n_evs < need_ev) {
+    cudaEvent_t* ev = new cudaEvent_t[need_ev];
+    int made = 0;
+    for (; made < need_ev && e == cudaSuccess; ++made) {
+      if (made < gp->n_evs) ev[made] = gp->evs[made];
+      else e = cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      for (int i = gp->n_evs; i < made - 1; ++i) cudaEventDestroy(ev[i]);
+      delete[] ev;
+      return cuda_fail(e, "cudaEventCreateWithFlags");
+    }
+    delete[] gp->evs;
+    gp->evs = ev;
+    gp->n_evs = need_ev;
+  }
+  cudaStream_t cs = gp->cstream;
+  cudaEvent_t* ev = gp->evs;  // [0] start, [1] gridded, [2] end, [3 + c] chunk c uploaded, [3 + nc + c] chunk c degridded
+  const size_t vb = (gp->desc.precision == GRID_PREC_F32 ? 8 : 4) * (size_t)a.P;
+  const size_t ob = 8 * (size_t)a.P;
+  const size_t grid_bytes = (size_t)a.P * a.G * a.G * 8;
+#define GB_TRY(x) do { e = (x); if (e != cudaSuccess) return cuda_fail(e, #x); } while (0)
+  GB_TRY(cudaEventRecord(ev[0], stream));
+  GB_TRY(cudaStreamWaitEvent(cs, ev[0], 0));
+  GB_TRY(cudaMemsetAsync(grid_dev, 0, grid_bytes, stream));
+  // upload chunk c on the copy stream while chunk c-1 is gridded on the caller's stream
+  for (long long c = 0; c < nc; ++c) {
+    const long long k0 = c * chunk, n = std::min<long long>(chunk, n_vis - k0);
+    GB_TRY(cudaMemcpyAsync(uv_dev + 2 * k0, uv_host + 2 * k0, (size_t)n * 16, cudaMemcpyHostToDevice, cs));
+    GB_TRY(cudaMemcpyAsync((char*)vis_dev + k0 * vb, (const char*)vis_host + k0 * vb, (size_t)n * vb,
+                           cudaMemcpyHostToDevice, cs));
+    if (weights_host)
+      GB_TRY(cudaMemcpyAsync(weights_dev + k0, weights_host + k0, (size_t)n * 4, cudaMemcpyHostToDevice, cs));
+    GB_TRY(cudaEventRecord(ev[3 + c], cs));
+    GB_TRY(cudaStreamWaitEvent(stream, ev[3 + c], 0));
+    rc = grid(gp, n, uv_dev + 2 * k0, (const char*)vis_dev + k0 * vb, weights_host ? weights_dev + k0 : nullptr,
+              kernel_table, grid_dev, stream);
+    if (rc) return rc;
+  }
+  // the grid goes down while it is degridded
+  GB_TRY(cudaEventRecord(ev[1], stream));
+  if (grid_host) {
+    GB_TRY(cudaStreamWaitEvent(cs, ev[1], 0));
+    GB_TRY(cudaMemcpyAsync(grid_host, grid_dev, grid_bytes, cudaMemcpyDeviceToHost, cs));
+  }
+  // degrid chunk c, then bring it down on the copy stream while chunk c+1 is degridded
+  for (long long c = 0; c < nc; ++c) {
+    const long long k0 = c * chunk, n = std::min<long long>(chunk, n_vis - k0);
+    rc = degrid(dp, n, uv_dev + 2 * k0, grid_dev, kernel_table, (char*)vis_out_dev + k0 * ob, stream);
+    if (rc) return rc;
+    GB_TRY(cudaEventRecord(ev[3 + nc + c], stream));
+    GB_TRY(cudaStreamWaitEvent(cs, ev[3 + nc + c], 0));
+    GB_TRY(cudaMemcpyAsync((char*)vis_out_host + k0 * ob, (const char*)vis_out_dev + k0 * ob, (size_t)n * ob,
+                           cudaMemcpyDeviceToHost, cs));
+  }
+  // later work on the caller's stream comes after every copy
+  GB_TRY(cudaEventRecord(ev[2], cs));
+  GB_TRY(cudaStreamWaitEvent(stream, ev[2], 0));
+#undef GB_TRY
   return GRID_OK;
 }
 
