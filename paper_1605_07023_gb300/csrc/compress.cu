@@ -7,7 +7,7 @@
 // Three passes over the records, in tiles of 1024 (one record per thread):
 //  1. head flags: record k starts a run unless it and k-1 both have a fine
 //     position and the two are equal on both axes. One bit per record (a warp
-//     ballot word) and one head count per tile.
+//     ballot word) and one head count per tile; four records per thread.
 //  2. one CTA scans the tile counts: tile offsets and the total.
 //  3. each record's run index = tile offset + heads before it in the tile
 //     (ballot prefix counts). A head copies its uv. The w*V of a run are
@@ -39,24 +39,52 @@ __device__ __forceinline__ bool fine_pair(double2 x, int log2O, int2& f) {
   return ok;
 }
 
+// Pass 1, 256 threads per tile of kTile records: thread t handles records
+// t, t + 256, t + 512 and t + 768 of the tile, so a warp covers 32
+// consecutive records at each step and its ballot is one flag word. The four
+// uv loads are issued together.
+constexpr int kFlagThreads = 256;
+constexpr int kFlagSteps = kTile / kFlagThreads;
+
 __global__ void compress_flags_kernel(const double2* __restrict__ uv, long long n, int log2O, unsigned* flags,
                                       int* tile_heads) {
-  const long long k = (long long)blockIdx.x * kTile + threadIdx.x;
+  const long long base = (long long)blockIdx.x * kTile + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int2 f = make_int2(0, 0);
-  bool ok = false;
-  if (k < n) ok = fine_pair(ld_stream(uv + k), log2O, f);
-  // the previous record's position: from the lane below, or loaded by lane 0
-  int2 fp;
-  fp.x = __shfl_up_sync(0xFFFFFFFFu, f.x, 1);
-  fp.y = __shfl_up_sync(0xFFFFFFFFu, f.y, 1);
-  bool okp = __shfl_up_sync(0xFFFFFFFFu, ok, 1);
-  if (lane == 0 && k > 0 && k < n) okp = fine_pair(uv[k - 1], log2O, fp);
-  const bool head = k < n && (k == 0 || !ok || !okp || f.x != fp.x || f.y != fp.y);
-  const unsigned word = __ballot_sync(0xFFFFFFFFu, head);
-  if (lane == 0 && k < n) flags[k >> 5] = word;
-  const int cnt = __syncthreads_count(head);
-  if (threadIdx.x == 0) tile_heads[blockIdx.x] = cnt;
+  double2 x[kFlagSteps];
+#pragma unroll
+  for (int i = 0; i < kFlagSteps; ++i) {
+    const long long k = base + i * kFlagThreads;
+    x[i] = k < n ? ld_stream(uv + k) : make_double2(0.0, 0.0);
+  }
+  int cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kFlagSteps; ++i) {
+    const long long k = base + i * kFlagThreads;
+    int2 f = make_int2(0, 0);
+    const bool ok = k < n && fine_pair(x[i], log2O, f);
+    // the previous record's position: from the lane below, or loaded by lane 0
+    int2 fp;
+    fp.x = __shfl_up_sync(0xFFFFFFFFu, f.x, 1);
+    fp.y = __shfl_up_sync(0xFFFFFFFFu, f.y, 1);
+    bool okp = __shfl_up_sync(0xFFFFFFFFu, ok, 1);
+    if (lane == 0 && k > 0 && k < n) okp = fine_pair(uv[k - 1], log2O, fp);
+    const bool head = k < n && (k == 0 || !ok || !okp || f.x != fp.x || f.y != fp.y);
+    const unsigned word = __ballot_sync(0xFFFFFFFFu, head);
+    if (lane == 0 && k < n) flags[k >> 5] = word;
+    cnt += head ? 1 : 0;
+  }
+  // head count of the tile
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, d);
+  __shared__ int warp_cnt[kFlagThreads / 32];
+  if (lane == 0) warp_cnt[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+#pragma unroll
+    for (int w = 0; w < kFlagThreads / 32; ++w) t += warp_cnt[w];
+    tile_heads[blockIdx.x] = t;
+  }
 }
 
 // Exclusive scan of the tile head counts by one CTA of kTile threads.
@@ -246,7 +274,7 @@ cudaError_t launch_compress(const Args& a, void* scratch, double2* uv_out, float
   float2* carry = (float2*)(tile_off + n_tiles);
   const long long want = (n_warps + 255) / 256;
   const unsigned fix_blocks = (unsigned)(want < (long long)sm_count * 4 ? want : (long long)sm_count * 4);
-  compress_flags_kernel<<<(unsigned)n_tiles, kTile, 0, st>>>(a.uv, n, a.g.log2O, flags, tile_heads);
+  compress_flags_kernel<<<(unsigned)n_tiles, kFlagThreads, 0, st>>>(a.uv, n, a.g.log2O, flags, tile_heads);
   compress_scan_kernel<<<1, kTile, 0, st>>>(tile_heads, n_tiles, tile_off, n_out);
   switch (a.g.P) {
     case 1:
