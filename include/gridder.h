@@ -267,6 +267,16 @@ typedef struct {
 
 int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu, int Bv, int max_S, int precision,
                       int vis_per_chunk, int threads);
+
+/*
+ * As grid_batch_create(), with two block shapes: items with S >= S_split use
+ * (Bu2, Bv2), the others (Bu, Bv). Larger supports favour larger blocks
+ * (Sec. 5: the best coarsening depends on the bin size). Built pairs: npol 1
+ * with (2,2)+(4,2) or (2,2)+(4,4), npol 4 with (2,2)+(4,2); (Bu2, Bv2) equal
+ * to (Bu, Bv) gives the one-shape kernel. S_split in 0..64 (0: one shape).
+ */
+int grid_batch_create_ex(grid_batch_t* out, int G, int oversample, int npol, int Bu, int Bv, int Bu2, int Bv2,
+                         int S_split, int max_S, int precision, int vis_per_chunk, int threads);
 int grid_batch_set(grid_batch_t batch, int n_items, const grid_batch_item* items);
 int grid_batch_execute(grid_batch_t batch, cudaStream_t stream);
 int grid_batch_skipped(grid_batch_t batch, int64_t* n_skipped, int reset);

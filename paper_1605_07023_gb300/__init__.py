@@ -298,11 +298,15 @@ class BatchPlan:
     """
 
     def __init__(self, G: int, oversample: int, npol: int, Bu: int = 2, Bv: int = 2, max_S: int = 15,
-                 precision: str = "f32", vis_per_chunk: int = 0, threads: int = 0):
+                 precision: str = "f32", vis_per_chunk: int = 0, threads: int = 0, Bu2: int | None = None,
+                 Bv2: int | None = None, S_split: int = 0):
+        """(Bu2, Bv2, S_split): items with S >= S_split use blocks of Bu2 x Bv2 (grid_batch_create_ex)."""
         lib = _lib.load()
         h = ctypes.c_void_p()
-        _lib.check(lib.grid_batch_create(ctypes.byref(h), G, oversample, npol, Bu, Bv, max_S, PREC[precision],
-                                         vis_per_chunk, threads), batch=True)
+        Bu2 = Bu if Bu2 is None else Bu2
+        Bv2 = Bv if Bv2 is None else Bv2
+        _lib.check(lib.grid_batch_create_ex(ctypes.byref(h), G, oversample, npol, Bu, Bv, Bu2, Bv2, S_split, max_S,
+                                            PREC[precision], vis_per_chunk, threads), batch=True)
         self._h = h
         self.G, self.oversample, self.npol, self.precision = G, oversample, npol, precision
         self._keep = []

@@ -24,7 +24,7 @@ EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "gr
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
            "grid_last_error", "grid_device_info", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
            "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
-           "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host")
+           "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host", "grid_batch_create_ex")
 
 
 class GridBatchItem(ctypes.Structure):
@@ -93,6 +93,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid_device_info.restype = i32
     lib.grid_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, i32, i32, i32]
     lib.grid_batch_create.restype = i32
+    lib.grid_batch_create_ex.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32]
+    lib.grid_batch_create_ex.restype = i32
     lib.grid_batch_set.argtypes = [vp, i32, ctypes.POINTER(GridBatchItem)]
     lib.grid_batch_set.restype = i32
     lib.grid_batch_execute.argtypes = [vp, vp]

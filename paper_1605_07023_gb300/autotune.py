@@ -164,3 +164,41 @@ def tune(G: int, S: int, oversample: int, npol: int, precision: str = "f32", n_v
         cache[key] = res
         save_cache(cache)
     return res
+
+
+# Batched gridding: one-shape kernels and the two-shape pairs the library builds
+BATCH_SHAPES = {1: [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3), (4, 2), (2, 4), (4, 4)],
+                4: [(1, 1), (2, 1), (2, 2), (4, 2)]}
+BATCH_PAIRS = {1: [((2, 2), (4, 2)), ((2, 2), (4, 4))], 4: [((2, 2), (4, 2))]}
+BATCH_SPLITS = (9, 11, 13)
+
+
+def tune_batch(G: int, oversample: int, npol: int, items, max_S: int, precision: str = "f32", reps: int = 2,
+               verbose: bool = False) -> dict:
+    """Fastest BatchPlan configuration for these items (each candidate set() and executed reps times).
+
+    Candidates: every one-shape kernel, and every two-shape pair with S_split in BATCH_SPLITS (only splits
+    that separate the items' supports). Returns the BatchPlan keyword arguments plus "ms". The items' grids
+    are left holding gridded data; zero them before use.
+    """
+    from . import BatchPlan, GridderError
+    supports = sorted({int(it["S"]) for it in items})
+    cands = [dict(Bu=bu, Bv=bv) for bu, bv in BATCH_SHAPES.get(npol, [])]
+    for (a, b) in BATCH_PAIRS.get(npol, []):
+        for split in BATCH_SPLITS:
+            if supports and supports[0] < split <= supports[-1]:
+                cands.append(dict(Bu=a[0], Bv=a[1], Bu2=b[0], Bv2=b[1], S_split=split))
+    best, best_ms = None, float("inf")
+    for cfg in cands:
+        try:
+            bp = BatchPlan(G, oversample, npol, max_S=max_S, precision=precision, **cfg)
+            bp.set(items)
+        except GridderError:
+            continue
+        ms = _time(bp.execute, reps)
+        if verbose:
+            print(f"batch {cfg}: {ms:.3f} ms", flush=True)
+        if ms < best_ms:
+            best, best_ms = dict(cfg, ms=ms), ms
+        bp.close()
+    return best

@@ -15,17 +15,22 @@ using namespace gbg;
 
 namespace gbg {
 
-#define GB_BATCH(BU, BV, P) {BU, BV, P, (const void*)&grid_batch_kernel<BU, BV, P>, &batch_smem_bytes<BU, BV, P>}
+#define GB_BATCH(BU, BV, P) \
+  {BU, BV, BU, BV, P, (const void*)&grid_batch_kernel<BU, BV, BU, BV, P>, &batch_smem_bytes<BU, BV, BU, BV, P>}
+#define GB_BATCH2(BU, BV, BU2, BV2, P) \
+  {BU, BV, BU2, BV2, P, (const void*)&grid_batch_kernel<BU, BV, BU2, BV2, P>, &batch_smem_bytes<BU, BV, BU2, BV2, P>}
 
 static const BatchKernelEntry kBatchKernels[] = {
     GB_BATCH(1, 1, 1), GB_BATCH(2, 1, 1), GB_BATCH(1, 2, 1), GB_BATCH(2, 2, 1), GB_BATCH(3, 3, 1), GB_BATCH(4, 2, 1),
     GB_BATCH(2, 4, 1), GB_BATCH(4, 4, 1), GB_BATCH(1, 1, 4), GB_BATCH(2, 1, 4), GB_BATCH(2, 2, 4), GB_BATCH(4, 2, 4),
+    // two shapes: small supports with 2x2 blocks, large ones with 4x2 (or 4x4)
+    GB_BATCH2(2, 2, 4, 2, 1), GB_BATCH2(2, 2, 4, 4, 1), GB_BATCH2(2, 2, 4, 2, 4),
 };
 
 }  // namespace gbg
 
 struct grid_batch_s {
-  int G, O, P, Bu, Bv, max_S, precision, chunk_len, threads, device;
+  int G, O, P, Bu, Bv, Bu2, Bv2, S_split, max_S, precision, chunk_len, threads, device;
   int nb_max, tpc_max;
   const BatchKernelEntry* k;
   size_t smem;
@@ -54,6 +59,11 @@ const char* grid_batch_last_error(void) { return b_err.c_str(); }
 
 int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu, int Bv, int max_S, int precision,
                       int vis_per_chunk, int threads) {
+  return grid_batch_create_ex(out, G, oversample, npol, Bu, Bv, Bu, Bv, 0, max_S, precision, vis_per_chunk, threads);
+}
+
+int grid_batch_create_ex(grid_batch_t* out, int G, int oversample, int npol, int Bu, int Bv, int Bu2, int Bv2,
+                         int S_split, int max_S, int precision, int vis_per_chunk, int threads) {
   b_err.clear();
   if (!out) return bfail(GRID_ERR_INVALID, "null out");
   *out = nullptr;
@@ -63,12 +73,15 @@ int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu
   if (precision < GRID_PREC_F32 || precision > GRID_PREC_F16) return bfail(GRID_ERR_INVALID, "bad precision");
   if (vis_per_chunk < 0 || vis_per_chunk > (1 << 20) || threads < 0 || threads > 1024)
     return bfail(GRID_ERR_INVALID, "bad vis_per_chunk or threads");
+  if (Bu2 == Bu && Bv2 == Bv) S_split = 0;
+  if (S_split < 0 || S_split > 64) return bfail(GRID_ERR_INVALID, "S_split must be 0..64");
   const BatchKernelEntry* k = nullptr;
   for (const auto& e : kBatchKernels)
-    if (e.bu == Bu && e.bv == Bv && e.p == npol) k = &e;
-  if (!k) return bfail(GRID_ERR_UNSUPPORTED, "no batched kernel built for this (Bu, Bv, npol)");
+    if (e.bu == Bu && e.bv == Bv && e.bu2 == Bu2 && e.bv2 == Bv2 && e.p == npol) k = &e;
+  if (!k) return bfail(GRID_ERR_UNSUPPORTED, "no batched kernel built for these block shapes and npol");
   grid_batch_s* b = new grid_batch_s;
-  b->G = G; b->O = oversample; b->P = npol; b->Bu = Bu; b->Bv = Bv; b->max_S = max_S; b->precision = precision;
+  b->G = G; b->O = oversample; b->P = npol; b->Bu = Bu; b->Bv = Bv; b->Bu2 = Bu2; b->Bv2 = Bv2; b->S_split = S_split;
+  b->max_S = max_S; b->precision = precision;
   b->chunk_len = vis_per_chunk ? vis_per_chunk : 256;
   b->k = k;
   cudaError_t e = cudaGetDevice(&b->device);
@@ -81,8 +94,9 @@ int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu
     return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
   }
   b->sm_count = prop.multiProcessorCount;
-  b->nb_max = std::max(nb_of(max_S, Bu), nb_of(max_S, Bv));
-  const int ts_max = (b->nb_max / Bu) * (b->nb_max / Bv);
+  b->nb_max = std::max(std::max(nb_of(max_S, Bu), nb_of(max_S, Bv)), std::max(nb_of(max_S, Bu2), nb_of(max_S, Bv2)));
+  const int ts_max = std::max((nb_of(max_S, Bu) / Bu) * (nb_of(max_S, Bv) / Bv),
+                              (nb_of(max_S, Bu2) / Bu2) * (nb_of(max_S, Bv2) / Bv2));
   int thr = threads ? threads : 256;
   thr = std::max(thr, ts_max);
   thr = std::min(thr, fa.maxThreadsPerBlock);
@@ -92,7 +106,7 @@ int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu
   }
   b->threads = thr;
   // record buffers for at most 32 teams per CTA (small-S items use part of the CTA)
-  const int ts_min = (nb_of(1, Bu) / Bu) * (nb_of(1, Bv) / Bv);
+  const int ts_min = std::min((nb_of(1, Bu) / Bu) * (nb_of(1, Bv) / Bv), (nb_of(1, Bu2) / Bu2) * (nb_of(1, Bv2) / Bv2));
   b->tpc_max = std::min(32, thr / ts_min);
   b->smem = k->smem(oversample, b->nb_max, b->tpc_max);
   const size_t smem_max = prop.sharedMemPerBlockOptin;
@@ -140,9 +154,11 @@ int grid_batch_set(grid_batch_t b, int n_items, const grid_batch_item* items) {
       return bfail(GRID_ERR_INVALID, "misaligned item pointer");
     const size_t vb = (b->precision == GRID_PREC_F32 ? 8 : 4) * (size_t)b->P;
     if ((uintptr_t)s.vis % (vb >= 16 ? 16 : vb)) return bfail(GRID_ERR_INVALID, "misaligned vis pointer");
-    hi[i] = BatchItem{(const double2*)s.uv, s.vis, s.weights, s.kernel_table, (float2*)s.grid, (long long)s.n_vis, s.S, 0};
-    const int nbu = nb_of(s.S, b->Bu), nbv = nb_of(s.S, b->Bv);
-    const int ts = (nbu / b->Bu) * (nbv / b->Bv);
+    const int shape = (b->S_split > 0 && s.S >= b->S_split) ? 1 : 0;
+    hi[i] = BatchItem{(const double2*)s.uv, s.vis, s.weights, s.kernel_table, (float2*)s.grid, (long long)s.n_vis, s.S, shape};
+    const int bu = shape ? b->Bu2 : b->Bu, bv = shape ? b->Bv2 : b->Bv;
+    const int nbu = nb_of(s.S, bu), nbv = nb_of(s.S, bv);
+    const int ts = (nbu / bu) * (nbv / bv);
     const int tpc = std::min(b->tpc_max, b->threads / ts);
     const long long nch = (s.n_vis + b->chunk_len - 1) / b->chunk_len;
     for (long long c = 0; c < nch; c += tpc) {

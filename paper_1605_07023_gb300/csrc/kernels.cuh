@@ -36,6 +36,7 @@ namespace gbg {
 
 constexpr unsigned kInvalid = 0xFFFFFFFFu;
 constexpr int kRB = 32;   // records per team per staged batch (gridding)
+constexpr int kRBB = 16;  // records per team per staged batch (batched gridding: smaller buffers, more CTAs)
 constexpr int kRBD = 8;   // records per team per batch (degridding; bounded by the reduction buffer)
 constexpr int kSlots = 8; // flush slots per warp (lanes parked per cooperative-flush round)
 
@@ -608,12 +609,12 @@ __device__ __forceinline__ void window_flush(bool need, unsigned key, float2 (&a
 // Staging: batch b of a team's chunk goes into shared memory. Each team
 // thread loads records l, l+ts, ... of the batch (Sec. 4: "each work-item
 // loads one visibility").
-template <int BU, int BV, int P>
+template <int BU, int BV, int P, int RB = kRB>
 __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long long vend, int b, int l, int4* meta,
                                             float2* vals) {
   const Geometry& g = a.g;
-  for (int r = l; r < kRB; r += g.ts) {
-    const long long k = vbeg + (long long)b * kRB + r;
+  for (int r = l; r < RB; r += g.ts) {
+    const long long k = vbeg + (long long)b * RB + r;
     int4 m;
     m.x = (int)kInvalid;
     float2 val[P];
@@ -1150,7 +1151,7 @@ struct BatchItem {
   float2* grid;
   long long n_vis;
   int S;
-  int pad;
+  int shape;  // block shape: 0 = (BU1, BV1), 1 = (BU2, BV2) of a two-shape kernel
 };
 
 struct BatchArgs {
@@ -1172,23 +1173,105 @@ __host__ __device__ inline SmemLayout batch_layout(int O, int nb_max, int tpc_ma
   size_t off = 0;
   L.tabU = off; off += align16((size_t)O * BU * nb_max * 4);
   L.tabV = off; off += align16((size_t)O * BV * nb_max * 4);
-  L.meta = off; off += align16((size_t)2 * tpc_max * kRB * 16);
-  L.vals = off; off += align16((size_t)2 * tpc_max * kRB * P * 8);
+  L.meta = off; off += align16((size_t)2 * tpc_max * kRBB * 16);
+  L.vals = off; off += align16((size_t)2 * tpc_max * kRBB * P * 8);
   L.total = off;
   return L;
 }
 
+// One work unit of the batched kernel (up to tpc chunks of one item) with
+// blocks of BU x BV cells. `loaded` caches which item's tables are in shared
+// memory (uniform across the CTA).
 template <int BU, int BV, int P>
-__global__ void grid_batch_kernel(BatchArgs b) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void batch_unit(const BatchArgs& b, const int4 u, const BatchItem& it, unsigned char* smem,
+                                           int& loaded) {
   const SmemLayout L = batch_layout<BU, BV, P>(b.O, b.nb_max, b.tpc_max);
   float* tabU = (float*)(smem + L.tabU);
   float* tabV = (float*)(smem + L.tabV);
   int4* meta = (int4*)(smem + L.meta);
   float2* vals = (float2*)(smem + L.vals);
+  const int nbat = (b.chunk_len + kRBB - 1) / kRBB;
+  Args a;
+  a.g.G = b.G; a.g.S = it.S; a.g.O = b.O; a.g.log2O = b.log2O; a.g.h = (it.S - 1) / 2; a.g.P = P;
+  finish_geometry(a.g, BU, BV);
+  a.g.tpc = min(b.tpc_max, (int)blockDim.x / a.g.ts);
+  a.n_vis = it.n_vis;
+  a.uv = it.uv;
+  a.vis = it.vis;
+  a.vis_fmt = b.fmt;
+  a.weights = it.weights;
+  a.table = it.table;
+  a.tab_fmt = b.fmt;
+  a.grid = it.grid;
+  a.chunk_len = b.chunk_len;
+  a.n_chunks = (it.n_vis + b.chunk_len - 1) / b.chunk_len;
+  a.warp_sync = 0;
+  a.skipped = b.skipped;
+  const Geometry& g = a.g;
+  if (u.x != loaded) {
+    build_table<BU>(tabU, a, g.nbu);
+    build_table<BV>(tabV, a, g.nbv);
+    loaded = u.x;
+    __syncthreads();
+  }
+  const int team = threadIdx.x / g.ts;
+  const int l = threadIdx.x - team * g.ts;
+  const bool active = team < u.z;  // u.z <= tpc chunks in this unit
+  const TeamPos tp = team_pos<BU, BV>(l, g);
+  const long long chunk = (long long)u.y + team;
+  const long long vbeg = chunk * b.chunk_len;
+  const long long vend = active ? min(vbeg + b.chunk_len, it.n_vis) : vbeg;
+  int4* const mt0 = meta + team * kRBB;
+  int4* const mt1 = meta + (b.tpc_max + team) * kRBB;
+  float2* const vl0 = vals + (size_t)team * kRBB * P;
+  float2* const vl1 = vals + (size_t)(b.tpc_max + team) * kRBB * P;
+  float2 acc[P][BV][BU];
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int j = 0; j < BV; ++j)
+#pragma unroll
+      for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
+  unsigned cur = kInvalid;
+  for (int bt = 0; bt < nbat; ++bt) {
+    int4* const mtb = (bt & 1) ? mt1 : mt0;
+    float2* const vlb = (bt & 1) ? vl1 : vl0;
+    if (team < g.tpc) stage_batch<BU, BV, P, kRBB>(a, vbeg, vend, bt, l, mtb, vlb);
+    __syncthreads();
+    if (active) {
+#pragma unroll 1
+      for (int r = 0; r < kRBB; ++r) {
+        const int4 m = mtb[r];
+        if (m.x == (int)kInvalid) continue;
+        int offu, offv;
+        const unsigned key = box_key(m, tp, g, offu, offv);
+        // the box moved: flush the old block, then start the new one with this
+        // visibility (the contribution is prepared by all lanes between the two)
+        const bool moved = key != cur;
+        if (moved && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+        Contribution<BU, BV, P> c;
+        c.prepare(offu, offv, vlb + r * P, tabU, tabV);
+        if (moved) {
+          cur = key;
+          c.template apply<false>(acc);
+        } else {
+          c.template apply<true>(acc);
+        }
+      }
+    }
+  }
+  if (active && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+}
+
+// Batched gridding (many grids in one persistent launch): CTAs take work
+// units from an atomic counter. Each item is gridded with block shape
+// (BU1, BV1) or, when its shape flag is set, (BU2, BV2): larger supports
+// favour larger blocks. A one-shape kernel has BU2 = BU1, BV2 = BV1.
+template <int BU1, int BV1, int BU2, int BV2, int P>
+__global__ void grid_batch_kernel(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_unit;
-  int loaded = -1;  // item whose tables are in shared memory (uniform across the CTA)
-  const int nbat = (b.chunk_len + kRB - 1) / kRB;
+  int loaded = -1;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_unit = atomicAdd(b.unit_next, 1);
@@ -1197,86 +1280,24 @@ __global__ void grid_batch_kernel(BatchArgs b) {
     if (unit >= b.n_units) break;
     const int4 u = b.units[unit];
     const BatchItem it = b.items[u.x];
-    Args a;
-    a.g.G = b.G; a.g.S = it.S; a.g.O = b.O; a.g.log2O = b.log2O; a.g.h = (it.S - 1) / 2; a.g.P = P;
-    finish_geometry(a.g, BU, BV);
-    a.g.tpc = min(b.tpc_max, (int)blockDim.x / a.g.ts);
-    a.n_vis = it.n_vis;
-    a.uv = it.uv;
-    a.vis = it.vis;
-    a.vis_fmt = b.fmt;
-    a.weights = it.weights;
-    a.table = it.table;
-    a.tab_fmt = b.fmt;
-    a.grid = it.grid;
-    a.chunk_len = b.chunk_len;
-    a.n_chunks = (it.n_vis + b.chunk_len - 1) / b.chunk_len;
-    a.warp_sync = 0;
-    a.skipped = b.skipped;
-    const Geometry& g = a.g;
-    if (u.x != loaded) {
-      build_table<BU>(tabU, a, g.nbu);
-      build_table<BV>(tabV, a, g.nbv);
-      loaded = u.x;
-      __syncthreads();
+    if constexpr (BU1 == BU2 && BV1 == BV2) {
+      batch_unit<BU1, BV1, P>(b, u, it, smem, loaded);
+    } else {
+      if (it.shape == 0) batch_unit<BU1, BV1, P>(b, u, it, smem, loaded);
+      else batch_unit<BU2, BV2, P>(b, u, it, smem, loaded);
     }
-    const int team = threadIdx.x / g.ts;
-    const int l = threadIdx.x - team * g.ts;
-    const bool active = team < u.z;  // u.z <= tpc chunks in this unit
-    const TeamPos tp = team_pos<BU, BV>(l, g);
-      const long long chunk = (long long)u.y + team;
-    const long long vbeg = chunk * b.chunk_len;
-    const long long vend = active ? min(vbeg + b.chunk_len, it.n_vis) : vbeg;
-    int4* const mt0 = meta + team * kRB;
-    int4* const mt1 = meta + (b.tpc_max + team) * kRB;
-    float2* const vl0 = vals + (size_t)team * kRB * P;
-    float2* const vl1 = vals + (size_t)(b.tpc_max + team) * kRB * P;
-    float2 acc[P][BV][BU];
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-#pragma unroll
-      for (int j = 0; j < BV; ++j)
-#pragma unroll
-        for (int i = 0; i < BU; ++i) acc[p][j][i] = make_float2(0.f, 0.f);
-    unsigned cur = kInvalid;
-    for (int bt = 0; bt < nbat; ++bt) {
-      int4* const mtb = (bt & 1) ? mt1 : mt0;
-      float2* const vlb = (bt & 1) ? vl1 : vl0;
-      if (team < g.tpc) stage_batch<BU, BV, P>(a, vbeg, vend, bt, l, mtb, vlb);
-      __syncthreads();
-      if (active) {
-#pragma unroll 1
-        for (int r = 0; r < kRB; ++r) {
-          const int4 m = mtb[r];
-          if (m.x == (int)kInvalid) continue;
-          int offu, offv;
-          const unsigned key = box_key(m, tp, g, offu, offv);
-          // the box moved: flush the old block, then start the new one with this
-          // visibility (the contribution is prepared by all lanes between the two)
-          const bool moved = key != cur;
-          if (moved && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
-          Contribution<BU, BV, P> c;
-          c.prepare(offu, offv, vlb + r * P, tabU, tabV);
-          if (moved) {
-            cur = key;
-            c.template apply<false>(acc);
-          } else {
-            c.template apply<true>(acc);
-          }
-        }
-      }
-    }
-    if (active && cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
   }
 }
 
-template <int BU, int BV, int P>
+template <int BU1, int BV1, int BU2, int BV2, int P>
 size_t batch_smem_bytes(int O, int nb_max, int tpc_max) {
-  return batch_layout<BU, BV, P>(O, nb_max, tpc_max).total;
+  const size_t a = batch_layout<BU1, BV1, P>(O, nb_max, tpc_max).total;
+  const size_t b = batch_layout<BU2, BV2, P>(O, nb_max, tpc_max).total;
+  return a > b ? a : b;
 }
 
 struct BatchKernelEntry {
-  int bu, bv, p;
+  int bu, bv, bu2, bv2, p;
   const void* fn;
   size_t (*smem)(int O, int nb_max, int tpc_max);
 };

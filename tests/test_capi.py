@@ -72,3 +72,19 @@ def test_desc_init_defaults(lib):
     lib.grid_plan_desc_init(ctypes.byref(d), 2048, 7, 8, 4, 2)
     assert (d.G, d.S, d.oversample, d.npol, d.Bu, d.Bv) == (2048, 7, 8, 4, 2, 2)
     assert d.precision == 0 and d.schedule == 0
+
+
+def test_newer_entry_points_reject_bad_arguments(lib):
+    from paper_1605_07023_gb300 import _lib
+    INV = _lib.GRID_ERR_INVALID
+    # pipelined host pass, compression and expansion: no plan
+    assert lib.grid_degrid_host(None, None, 0, None, None, None, None, None, None, None, None, None, None, None, 0,
+                                None) == INV
+    assert lib.grid_compress(None, 0, None, None, None, None, None, None, None, None) == INV
+    assert lib.degrid_expand(None, 0, None, 0, None, None, None, None) == INV
+    # two-shape batches: bad grid side, bad split, and shapes with no kernel
+    h = ctypes.c_void_p()
+    assert lib.grid_batch_create_ex(ctypes.byref(h), 3, 8, 1, 2, 2, 4, 2, 13, 15, 0, 0, 0) == INV
+    assert lib.grid_batch_create_ex(ctypes.byref(h), 1024, 8, 1, 2, 2, 4, 2, 99, 15, 0, 0, 0) == INV
+    assert lib.grid_batch_create_ex(ctypes.byref(h), 1024, 8, 1, 2, 2, 8, 8, 13, 15, 0, 0, 0) == _lib.GRID_ERR_UNSUPPORTED
+    assert not h.value

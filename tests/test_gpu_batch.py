@@ -50,6 +50,21 @@ def test_batch_matches_oracle(gb, B):
     assert bp.skipped() == 0
 
 
+@pytest.mark.parametrize("shapes", [((2, 2), (4, 2), 13), ((2, 2), (4, 4), 11)])
+def test_batch_two_shapes_matches_oracle(gb, shapes):
+    (bu, bv), (bu2, bv2), split = shapes
+    ws = [w for row in small_batch(n_chan=2, total=400_000, seed=4) for w in row]
+    assert {w.S for w in ws} >= {7, 15} and any(w.S >= split for w in ws) and any(w.S < split for w in ws)
+    items = device_items(ws)
+    bp = gb.BatchPlan(1024, 8, 1, Bu=bu, Bv=bv, Bu2=bu2, Bv2=bv2, S_split=split, max_S=15)
+    bp.set(items)
+    bp.execute()
+    torch.cuda.synchronize()
+    for w, it in zip(ws, items):
+        ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
+        assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, (w.name, shapes)
+
+
 def test_batch_cuda_graph_replay(gb):
     ws = [w for row in small_batch(n_chan=2, total=300_000, seed=1) for w in row]
     items = device_items(ws)
@@ -91,3 +106,21 @@ def test_batch_empty_and_invalid(gb):
     with pytest.raises(gb.GridderError):
         bad = dict(items[0], S=9)      # S above max_S
         bp.set([bad])
+
+
+def test_batch_autotuner_picks_a_working_plan(gb):
+    from paper_1605_07023_gb300 import autotune
+    ws = [w for row in small_batch(n_chan=1, total=200_000, seed=5) for w in row]
+    items = device_items(ws)
+    best = autotune.tune_batch(1024, 8, 1, items, max_S=15, reps=1)
+    assert best is not None and best["ms"] > 0
+    cfg = {k: v for k, v in best.items() if k != "ms"}
+    for it in items:
+        it["grid"].zero_()
+    bp = gb.BatchPlan(1024, 8, 1, max_S=15, **cfg)
+    bp.set(items)
+    bp.execute()
+    torch.cuda.synchronize()
+    for w, it in zip(ws, items):
+        ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
+        assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, (w.name, cfg)
