@@ -382,9 +382,10 @@ def main():
         except Exception:
             traffic = None
 
-    # ---- e2e through the C ABI from pinned host buffers: grid_degrid_host() zeroes the grid, uploads
-    # uv, values and weights, grids, degrids and downloads the grid and the degridded values, with the
-    # copies overlapped with the kernels (all inside the timed region)
+    # ---- e2e through the C ABI from pinned host buffers: grid_degrid_host_steps() runs the timed steps
+    # in one call; each step zeroes the grid, uploads uv, values and weights, grids, degrids and downloads
+    # the grid and the degridded values. Copies overlap the kernels and the next step's uploads overlap
+    # this step's downloads; every byte of every step crosses the link inside the timed region.
     e2e = None
     if not args.no_e2e:
         h_uv = torch.from_numpy(w.uv).pin_memory()
@@ -394,25 +395,25 @@ def main():
         h_out = torch.empty((w.n_vis, w.npol), dtype=torch.complex64).pin_memory()
         h2d = h_uv.numel() * 8 + h_vis.numel() * 8 + h_wt.numel() * 4
         d2h = h_grid.numel() * 8 + h_out.numel() * 8
-        work = (uv, vis, wt, vis_out)
+        work = [(uv, vis, wt, vis_out), (torch.empty_like(uv), torch.empty_like(vis), torch.empty_like(wt),
+                                         torch.empty_like(vis_out))]
 
-        def e2e_step():
-            gb.grid_degrid_host(gplan, dplan, h_uv, h_vis, h_wt, table, grid_buf, h_out, h_grid, work=work,
-                                stream=stream)
+        def e2e_steps(k):
+            # k passes in one call: step s+1's uploads overlap step s's degridding and downloads
+            steps = [dict(uv=h_uv, vis=h_vis, weights=h_wt, vis_out=h_out, grid_out=h_grid) for _ in range(k)]
+            gb.grid_degrid_host_steps(gplan, dplan, steps, table, grid_buf, work=work, stream=stream)
 
-        for _ in range(args.warmup):
-            e2e_step()
+        e2e_steps(max(args.warmup, 1))
         barrier(world)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_steps(args.steps)
         torch.cuda.synchronize()
         et = max_over_ranks(time.perf_counter() - t, world)
         barrier(world)
         e2e = {"value": taps_all * args.steps / et, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * et / args.steps,
-               "api": "grid_degrid_host (C ABI, pinned host buffers, copies overlapped with the kernels)"}
+               "api": "grid_degrid_host_steps (C ABI, pinned host buffers; uploads, kernels and downloads overlapped within and across steps)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

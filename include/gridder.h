@@ -221,6 +221,32 @@ int grid_degrid_host(grid_plan_t gplan, grid_plan_t dplan, int64_t n_vis, const 
                      const void* kernel_table, void* grid_dev, void* vis_out_host, void* grid_host, int64_t chunk,
                      cudaStream_t stream);
 
+/* One step of grid_degrid_host_steps: its pinned host inputs and outputs. */
+typedef struct {
+  const double* uv_host;    /* [n][2] f64 */
+  const void* vis_host;     /* [n][npol], plan precision */
+  const float* weights_host; /* [n] f32, or NULL (all steps alike) */
+  void* vis_out_host;       /* [n][npol] complex64: degridded values (unweighted) */
+  void* grid_host;          /* [npol][G][G] complex64, or NULL */
+} grid_host_step;
+
+/*
+ * A sequence of n_steps passes of grid_degrid_host() (each: zero the grid,
+ * grid the step's visibilities, degrid them), pipelined ACROSS steps: the
+ * uploads of step s+1 run while step s degrids and downloads. Two device work
+ * sets alternate between steps: uv_dev[2], vis_dev[2], weights_dev[2] (NULL
+ * array when unweighted) and vis_out_dev[2], each with room for n
+ * visibilities. Uploads go on one copy stream and downloads on another,
+ * ordered by events; the grid is shared and rezeroed per step once the
+ * previous step's grid went down. Every step has n visibilities. n_steps in
+ * 0..64, at most 64 chunks per step. Ordering with `stream` as for
+ * grid_degrid_host(). Returns GRID_OK or a negative error code.
+ */
+int grid_degrid_host_steps(grid_plan_t gplan, grid_plan_t dplan, int n_steps, const grid_host_step* steps,
+                           int64_t n_vis, double* const* uv_dev, void* const* vis_dev, float* const* weights_dev,
+                           void* const* vis_out_dev, const void* kernel_table, void* grid_dev, int64_t chunk,
+                           cudaStream_t stream);
+
 /*
  * Expansion after degridding compressed records: every member of a run has
  * the run's fine position, so its degridded value is the run's.

@@ -261,6 +261,42 @@ def grid_degrid_host(gplan: Plan, dplan: Plan, uv_host, vis_host, weights_host, 
     return vis_out_host
 
 
+def grid_degrid_host_steps(gplan: Plan, dplan: Plan, steps, kernel_table, grid, work=None, chunk: int = 0, stream=None):
+    """grid_degrid_host_steps(): several grid + degrid passes from pinned host buffers, pipelined across steps.
+
+    steps: list of dicts with host tensors uv, vis, weights (or None), vis_out, grid_out (or None); every step
+    has the same visibility count. work: two tuples (uv_dev, vis_dev, weights_dev, vis_out_dev), allocated here
+    if None. The host outputs are complete once the stream reaches the end of the call.
+    """
+    torch = _torch()
+    if not steps:
+        return
+    n = steps[0]["uv"].shape[0]
+    dev = grid.device
+    if work is None:
+        s0 = steps[0]
+        work = [(torch.empty((n, 2), dtype=torch.float64, device=dev), torch.empty_like(s0["vis"], device=dev),
+                 None if s0["weights"] is None else torch.empty_like(s0["weights"], device=dev),
+                 torch.empty((n, gplan.npol), dtype=torch.complex64, device=dev)) for _ in range(2)]
+    arr = (_lib.GridHostStep * len(steps))()
+    for i, st in enumerate(steps):
+        if st["uv"].shape[0] != n or st["vis"].shape[0] != n or st["vis_out"].shape[0] != n:
+            raise ValueError("every step must have the same number of visibilities")
+        arr[i] = _lib.GridHostStep(_hptr(st["uv"], "uv", torch.float64), _hptr(st["vis"], "vis", _vis_dtype(gplan)),
+                                   _hptr(st["weights"], "weights", torch.float32) or None,
+                                   _hptr(st["vis_out"], "vis_out", torch.complex64),
+                                   _hptr(st.get("grid_out"), "grid_out", torch.complex64) or None)
+    P2 = ctypes.c_void_p * 2
+    uv_d = P2(*[_dptr(wk[0], "uv_dev", torch.float64, 2) for wk in work])
+    vis_d = P2(*[_dptr(wk[1], "vis_dev", _vis_dtype(gplan)) for wk in work])
+    wt_d = None if work[0][2] is None else P2(*[_dptr(wk[2], "weights_dev", torch.float32, 1) for wk in work])
+    out_d = P2(*[_dptr(wk[3], "vis_out_dev", torch.complex64, 2) for wk in work])
+    _lib.check(_lib.load().grid_degrid_host_steps(
+        gplan.handle, dplan.handle, len(steps), arr, n, uv_d, vis_d, wt_d, out_d,
+        _dptr(kernel_table, "kernel_table", (torch.float32, torch.bfloat16, torch.float16), 2),
+        _dptr(grid, "grid", torch.complex64, 3), int(chunk), _stream_ptr(stream)))
+
+
 def grid_make_kernel_table(S: int, oversample: int, beta: float, precision: str = "f32", device=None, stream=None):
     """Oversampled Kaiser-Bessel table [O, S], computed on the device in FP64 and rounded once."""
     torch = _torch()

@@ -24,7 +24,13 @@ EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "gr
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
            "grid_last_error", "grid_device_info", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
            "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
-           "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host", "grid_batch_create_ex")
+           "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host", "grid_batch_create_ex",
+           "grid_degrid_host_steps")
+
+
+class GridHostStep(ctypes.Structure):
+    _fields_ = [("uv_host", ctypes.c_void_p), ("vis_host", ctypes.c_void_p), ("weights_host", ctypes.c_void_p),
+                ("vis_out_host", ctypes.c_void_p), ("grid_host", ctypes.c_void_p)]
 
 
 class GridBatchItem(ctypes.Structure):
@@ -87,6 +93,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.degrid_expand.restype = i32
     lib.grid_degrid_host.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
     lib.grid_degrid_host.restype = i32
+    lib.grid_degrid_host_steps.argtypes = [vp, vp, i32, ctypes.POINTER(GridHostStep), i64, ctypes.POINTER(vp),
+                                           ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, i64, vp]
+    lib.grid_degrid_host_steps.restype = i32
     lib.grid_last_error.argtypes = []
     lib.grid_last_error.restype = ctypes.c_char_p
     lib.grid_device_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]

@@ -30,7 +30,8 @@ struct grid_plan_s {
   void* cs_buf;             // compression scratch (grow-only)
   size_t cs_bytes;
   cudaStream_t cstream;     // copy stream of grid_degrid_host (created on first use)
-  cudaEvent_t* evs;         // its events (grow-only)
+  cudaStream_t dstream;     // download stream of grid_degrid_host_steps (created on first use)
+  cudaEvent_t* evs;         // their events (grow-only)
   int n_evs;
 };
 
@@ -116,6 +117,31 @@ Args make_args(const grid_plan_s* pl, int64_t n_vis, const double* uv) {
   a.tab_fmt = pl->desc.precision;
   a.warp_sync = pl->warp_sync;
   return a;
+}
+
+// At least n events in the plan's pool (grow-only; created without timing).
+int ensure_events(grid_plan_s* pl, int n) {
+  if (pl->n_evs >= n) return GRID_OK;
+  cudaEvent_t* ev = new cudaEvent_t[n];
+  cudaError_t e = cudaSuccess;
+  int made = 0;
+  for (; made < n; ++made) {
+    if (made < pl->n_evs) {
+      ev[made] = pl->evs[made];
+    } else {
+      e = cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming);
+      if (e != cudaSuccess) break;
+    }
+  }
+  if (e != cudaSuccess) {
+    for (int i = pl->n_evs; i < made; ++i) cudaEventDestroy(ev[i]);
+    delete[] ev;
+    return cuda_fail(e, "cudaEventCreateWithFlags");
+  }
+  delete[] pl->evs;
+  pl->evs = ev;
+  pl->n_evs = n;
+  return GRID_OK;
 }
 
 int check_device(const grid_plan_s* pl) {
@@ -270,6 +296,7 @@ void grid_plan_destroy(grid_plan_t pl) {
   for (int i = 0; i < pl->n_evs; ++i) cudaEventDestroy(pl->evs[i]);
   delete[] pl->evs;
   if (pl->cstream) cudaStreamDestroy(pl->cstream);
+  if (pl->dstream) cudaStreamDestroy(pl->dstream);
   cudaFree(pl->d_skipped);
   delete pl;
 }
@@ -483,22 +510,8 @@ int grid_degrid_host(grid_plan_t gp, grid_plan_t dp, int64_t n_vis, const double
   cudaError_t e = cudaSuccess;
   if (!gp->cstream) e = cudaStreamCreateWithFlags(&gp->cstream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
-  if (gp->n_evs < need_ev) {
-    cudaEvent_t* ev = new cudaEvent_t[need_ev];
-    int made = 0;
-    for (; made < need_ev && e == cudaSuccess; ++made) {
-      if (made < gp->n_evs) ev[made] = gp->evs[made];
-      else e = cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming);
-    }
-    if (e != cudaSuccess) {
-      for (int i = gp->n_evs; i < made - 1; ++i) cudaEventDestroy(ev[i]);
-      delete[] ev;
-      return cuda_fail(e, "cudaEventCreateWithFlags");
-    }
-    delete[] gp->evs;
-    gp->evs = ev;
-    gp->n_evs = need_ev;
-  }
+  rc = ensure_events(gp, need_ev);
+  if (rc) return rc;
   cudaStream_t cs = gp->cstream;
   cudaEvent_t* ev = gp->evs;  // [0] start, [1] gridded, [2] end, [3 + c] chunk c uploaded, [3 + nc + c] chunk c degridded
   const size_t vb = (gp->desc.precision == GRID_PREC_F32 ? 8 : 4) * (size_t)a.P;
@@ -541,6 +554,105 @@ int grid_degrid_host(grid_plan_t gp, grid_plan_t dp, int64_t n_vis, const double
   // later work on the caller's stream comes after every copy
   GB_TRY(cudaEventRecord(ev[2], cs));
   GB_TRY(cudaStreamWaitEvent(stream, ev[2], 0));
+#undef GB_TRY
+  return GRID_OK;
+}
+
+int grid_degrid_host_steps(grid_plan_t gp, grid_plan_t dp, int n_steps, const grid_host_step* steps, int64_t n_vis,
+                           double* const* uv_dev, void* const* vis_dev, float* const* weights_dev,
+                           void* const* vis_out_dev, const void* kernel_table, void* grid_dev, int64_t chunk,
+                           cudaStream_t stream) {
+  g_err.clear();
+  if (!gp || !dp) return fail(GRID_ERR_INVALID, "null plan");
+  const Geometry &a = gp->g, &b = dp->g;
+  if (a.G != b.G || a.S != b.S || a.O != b.O || a.P != b.P || gp->desc.precision != dp->desc.precision)
+    return fail(GRID_ERR_INVALID, "the two plans differ in G, S, oversample, npol or precision");
+  if (n_steps < 0 || n_steps > 64 || (n_steps > 0 && !steps)) return fail(GRID_ERR_INVALID, "n_steps=%d (0..64)", n_steps);
+  if (n_vis < 0 || n_vis > ((int64_t)1 << 40)) return fail(GRID_ERR_INVALID, "n_vis=%lld out of range", (long long)n_vis);
+  if (!kernel_table || !grid_dev) return fail(GRID_ERR_INVALID, "null kernel_table or grid");
+  if (chunk < 0) return fail(GRID_ERR_INVALID, "chunk=%lld", (long long)chunk);
+  if (n_steps == 0) return GRID_OK;
+  if (!uv_dev || !vis_dev || !vis_out_dev) return fail(GRID_ERR_INVALID, "null work-buffer arrays");
+  bool weighted = false;
+  for (int st = 0; st < n_steps; ++st) {
+    const grid_host_step& h = steps[st];
+    if (n_vis > 0 && (!h.uv_host || !h.vis_host || !h.vis_out_host)) return fail(GRID_ERR_INVALID, "step %d: null host buffer", st);
+    if (st > 0 && (h.weights_host != nullptr) != weighted) return fail(GRID_ERR_INVALID, "steps must all have weights or none");
+    weighted = h.weights_host != nullptr;
+  }
+  for (int w = 0; w < 2; ++w)
+    if (n_vis > 0 && (!uv_dev[w] || !vis_dev[w] || !vis_out_dev[w] || (weighted && (!weights_dev || !weights_dev[w]))))
+      return fail(GRID_ERR_INVALID, "null device work buffer in set %d", w);
+  int rc = check_device(gp);
+  if (rc) return rc;
+  if (chunk == 0) chunk = 1 << 20;
+  const long long nc = n_vis > 0 ? (n_vis + chunk - 1) / chunk : 0;
+  if (nc > 64) return fail(GRID_ERR_INVALID, "%lld chunks: use a larger chunk (at most 64 per step)", nc);
+  cudaError_t e = cudaSuccess;
+  if (!gp->cstream) e = cudaStreamCreateWithFlags(&gp->cstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !gp->dstream) e = cudaStreamCreateWithFlags(&gp->dstream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+  // events per step: uploaded chunks, degridded chunks, gridded, grid down, inputs free, outputs down; plus start
+  const int per = (int)(2 * nc + 4);
+  rc = ensure_events(gp, 1 + per * n_steps);
+  if (rc) return rc;
+  cudaEvent_t* ev = gp->evs;
+  auto E = [&](int st, int k) { return ev[1 + st * per + k]; };  // k: 0..nc-1 up, nc..2nc-1 degridded, then 4 more
+  const int kG = (int)(2 * nc), kGD = kG + 1, kFree = kG + 2, kDown = kG + 3;
+  cudaStream_t up = gp->cstream, down = gp->dstream;
+  const size_t vb = (gp->desc.precision == GRID_PREC_F32 ? 8 : 4) * (size_t)a.P;
+  const size_t ob = 8 * (size_t)a.P;
+  const size_t grid_bytes = (size_t)a.P * a.G * a.G * 8;
+#define GB_TRY(x) do { e = (x); if (e != cudaSuccess) return cuda_fail(e, #x); } while (0)
+  GB_TRY(cudaEventRecord(ev[0], stream));
+  GB_TRY(cudaStreamWaitEvent(up, ev[0], 0));
+  GB_TRY(cudaStreamWaitEvent(down, ev[0], 0));
+  for (int st = 0; st < n_steps; ++st) {
+    const grid_host_step& h = steps[st];
+    const int w = st & 1;
+    // uploads into work set w once step st-2 no longer reads it
+    if (st >= 2) GB_TRY(cudaStreamWaitEvent(up, E(st - 2, kFree), 0));
+    for (long long c = 0; c < nc; ++c) {
+      const long long k0 = c * chunk, n = std::min<long long>(chunk, n_vis - k0);
+      GB_TRY(cudaMemcpyAsync(uv_dev[w] + 2 * k0, h.uv_host + 2 * k0, (size_t)n * 16, cudaMemcpyHostToDevice, up));
+      GB_TRY(cudaMemcpyAsync((char*)vis_dev[w] + k0 * vb, (const char*)h.vis_host + k0 * vb, (size_t)n * vb,
+                             cudaMemcpyHostToDevice, up));
+      if (weighted)
+        GB_TRY(cudaMemcpyAsync(weights_dev[w] + k0, h.weights_host + k0, (size_t)n * 4, cudaMemcpyHostToDevice, up));
+      GB_TRY(cudaEventRecord(E(st, (int)c), up));
+    }
+    // the grid is reused: wait until the previous step's grid went down
+    if (st >= 1) GB_TRY(cudaStreamWaitEvent(stream, E(st - 1, kGD), 0));
+    GB_TRY(cudaMemsetAsync(grid_dev, 0, grid_bytes, stream));
+    for (long long c = 0; c < nc; ++c) {
+      const long long k0 = c * chunk, n = std::min<long long>(chunk, n_vis - k0);
+      GB_TRY(cudaStreamWaitEvent(stream, E(st, (int)c), 0));
+      rc = grid(gp, n, uv_dev[w] + 2 * k0, (const char*)vis_dev[w] + k0 * vb, weighted ? weights_dev[w] + k0 : nullptr,
+                kernel_table, grid_dev, stream);
+      if (rc) return rc;
+    }
+    GB_TRY(cudaEventRecord(E(st, kG), stream));
+    GB_TRY(cudaStreamWaitEvent(down, E(st, kG), 0));
+    if (h.grid_host) GB_TRY(cudaMemcpyAsync(h.grid_host, grid_dev, grid_bytes, cudaMemcpyDeviceToHost, down));
+    GB_TRY(cudaEventRecord(E(st, kGD), down));
+    // degrid into output set w once step st-2's outputs went down
+    if (st >= 2) GB_TRY(cudaStreamWaitEvent(stream, E(st - 2, kDown), 0));
+    for (long long c = 0; c < nc; ++c) {
+      const long long k0 = c * chunk, n = std::min<long long>(chunk, n_vis - k0);
+      rc = degrid(dp, n, uv_dev[w] + 2 * k0, grid_dev, kernel_table, (char*)vis_out_dev[w] + k0 * ob, stream);
+      if (rc) return rc;
+      GB_TRY(cudaEventRecord(E(st, (int)(nc + c)), stream));
+      GB_TRY(cudaStreamWaitEvent(down, E(st, (int)(nc + c)), 0));
+      GB_TRY(cudaMemcpyAsync((char*)h.vis_out_host + k0 * ob, (const char*)vis_out_dev[w] + k0 * ob, (size_t)n * ob,
+                             cudaMemcpyDeviceToHost, down));
+    }
+    GB_TRY(cudaEventRecord(E(st, kFree), stream));
+    GB_TRY(cudaEventRecord(E(st, kDown), down));
+  }
+  // later work on the caller's stream comes after every copy
+  GB_TRY(cudaStreamWaitEvent(stream, E(n_steps - 1, kDown), 0));
+  GB_TRY(cudaEventRecord(ev[0], up));
+  GB_TRY(cudaStreamWaitEvent(stream, ev[0], 0));
 #undef GB_TRY
   return GRID_OK;
 }

@@ -138,38 +138,9 @@ __device__ __forceinline__ double2 ld_stream(const double2* p) {
                : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(policy_stream()));
   return v;
 }
-__device__ __forceinline__ float4 ld_stream(const float4* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(policy_stream()));
-  return v;
-}
-__device__ __forceinline__ float2 ld_stream(const float2* p) {
-  float2 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-               : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(policy_stream()));
-  return v;
-}
 __device__ __forceinline__ float ld_stream(const float* p) {
   float v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy_stream()));
-  return v;
-}
-__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(policy_stream()));
-  return v;
-}
-__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
-  uint2 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-               : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(policy_stream()));
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy_stream()));
   return v;
 }
 // output visibilities (degridding): written once
@@ -386,12 +357,10 @@ template <int BU, int BV, int P>
 __host__ __device__ inline SmemLayout degrid_layout(const Geometry& g, int nthreads, int win) {
   SmemLayout L{};
   size_t off = 0;
-  const int tsp = g.ts | 1;
   L.tabU = off; off += align16((size_t)g.O * BU * g.nbu * 4);
   L.tabV = off; off += align16((size_t)g.O * BV * g.nbv * 4);
   L.meta = off; off += align16((size_t)2 * g.tpc * kRBD * 16);
   L.red = off; off += align16((size_t)g.tpc * degrid_team_stride(g.ts, P) * 4);
-  (void)tsp;
   (void)nthreads;
   (void)win;
   L.total = off;
