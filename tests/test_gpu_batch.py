@@ -124,3 +124,19 @@ def test_batch_autotuner_picks_a_working_plan(gb):
     for w, it in zip(ws, items):
         ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
         assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, (w.name, cfg)
+
+
+def test_full_batching_workload(gb):
+    """The whole batching workload (64 channels x 8 w-planes, 20 M visibilities, S by plane) in one
+    launch with the tuned one-shape plan; every grid checked against the oracle."""
+    ws = [w for row in synth.batched() for w in row]
+    assert len(ws) == 512 and abs(sum(w.n_vis for w in ws) - 20_000_000) < 1000
+    items = device_items(ws)
+    bp = gb.BatchPlan(1024, 8, 1, Bu=2, Bv=2, max_S=15)
+    bp.set(items)
+    bp.execute()
+    torch.cuda.synchronize()
+    assert bp.skipped() == 0
+    for w, it in zip(ws, items):
+        ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
+        assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, w.name

@@ -21,6 +21,7 @@ TOL = 1e-5
 
 
 @functools.lru_cache(maxsize=None)
+@functools.lru_cache(maxsize=1)
 def quad_pol():
     return synth.quad_pol()
 
@@ -285,3 +286,22 @@ def test_full_quad_pol(gb, schedule, B):
     """All 8,257,536 visibilities, in the launch configurations the benchmark times."""
     w = quad_pol()
     check_grid(gb, w, *B, schedule)
+
+
+def test_full_quad_pol_bench_launch_configs(gb):
+    """All 8,257,536 visibilities in the configurations the bench tunes to and times: gridding with
+    2x2 blocks, 128 visibilities per team and 128-thread CTAs, the plain Romein kernel (B=1, 1024 per
+    team), and degridding with 2x2 blocks, 64 per team and 256-thread CTAs (checked against the
+    oracle's adjoint of the GPU grid)."""
+    w = quad_pol()
+    check_grid(gb, w, 2, 2, "chunked", vis_per_chunk=128, threads=128)
+    check_grid(gb, w, 1, 1, "chunked", vis_per_chunk=1024)
+    table32 = kb32(w.S, w.oversample)
+    gplan = gb.Plan(w.G, w.S, w.oversample, w.npol, Bu=2, Bv=2, vis_per_chunk=128, threads=128)
+    got_grid = run_grid(gb, w, gplan, table32)
+    dplan = gb.Plan(w.G, w.S, w.oversample, w.npol, Bu=2, Bv=2, vis_per_chunk=64, threads=256)
+    uv, _, _, tab = to_dev(w, table32)
+    dv = gb.degrid(dplan, uv, torch.from_numpy(got_grid.astype(np.complex64)).cuda(), tab).cpu().numpy()
+    ref, _ = oracle.degrid(w.G, w.S, w.oversample, w.uv, got_grid.astype(np.complex64).astype(np.complex128), table32)
+    for p in range(w.npol):
+        assert rel_l2(dv[:, p], ref[:, p]) <= TOL
