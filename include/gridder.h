@@ -29,9 +29,15 @@
  *    - kernel_table: [O][S] real, float32, or bf16 / fp16 to match the
  *      plan's precision.
  *    - grid: [npol][G][G] complex64, row index v, column index u.
- *  - Every data pointer is a caller-owned DEVICE pointer. It is borrowed until
- *    the work queued on `stream` completes. Calls are asynchronous on
- *    `stream`; a device fault surfaces at the caller's next synchronisation.
+ *  - Every data pointer is a caller-owned DEVICE pointer, except the *_host
+ *    buffers of grid_degrid_host and grid_degrid_host_steps (pinned host
+ *    memory). Pointers are borrowed until the work queued on `stream`
+ *    completes. Calls are asynchronous on `stream`; a device fault surfaces
+ *    at the caller's next synchronisation.
+ *  - Threads: different plans (and batches) are independent. One plan must not
+ *    be used by several host threads at once (its scratch, skipped counter,
+ *    copy streams and events are shared by its calls). Error messages are
+ *    per host thread.
  *  - Return value: GRID_OK (0) or a negative GRID_ERR_* code. The message of
  *    the last error on the calling thread is in grid_last_error(). Nothing
  *    aborts the process.
@@ -56,7 +62,7 @@ enum {
   GRID_ERR_CUDA = -4         /* a CUDA runtime call or kernel launch failed */
 };
 
-/* Storage precision of vis and kernel_table (NEXT-1). Accumulation is always FP32. */
+/* Storage precision of vis and kernel_table. Accumulation is always FP32. */
 enum { GRID_PREC_F32 = 0, GRID_PREC_BF16 = 1, GRID_PREC_F16 = 2 };
 
 /* Work distribution. */

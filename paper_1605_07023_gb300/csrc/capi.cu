@@ -376,6 +376,7 @@ int degrid_weighted(grid_plan_t pl, int64_t n_vis, const double* uv, const void*
   if (!uv || !vis) return fail(GRID_ERR_INVALID, "null uv or vis");
   if (!aligned(uv, 16) || !aligned(vis, 8)) return fail(GRID_ERR_INVALID, "uv must be 16-byte and vis 8-byte aligned");
   if (weights && !aligned(weights, 4)) return fail(GRID_ERR_INVALID, "weights must be 4-byte aligned");
+  if ((n_vis + pl->chunk_len - 1) / pl->chunk_len > 0x7FFFFFFFLL) return fail(GRID_ERR_INVALID, "too many chunks");
   int rc = check_device(pl);
   if (rc) return rc;
   Args a = make_args(pl, n_vis, uv);
@@ -408,6 +409,7 @@ int grid_compute_indices(grid_plan_t pl, int64_t n_vis, const double* uv, int32_
   if (n_vis == 0) return GRID_OK;
   if (!uv || !cell || !sub) return fail(GRID_ERR_INVALID, "null pointer");
   if (!aligned(uv, 16) || !aligned(cell, 8) || !aligned(sub, 8)) return fail(GRID_ERR_INVALID, "misaligned pointer");
+  if ((n_vis + 255) / 256 > 0x7FFFFFFFLL) return fail(GRID_ERR_INVALID, "too many visibilities for one launch");
   int rc = check_device(pl);
   if (rc) return rc;
   Args a = make_args(pl, n_vis, uv);
