@@ -1,0 +1,34 @@
+"""The benchmark's JSON line contract, checked on the CPU through the reference arm (the oracle timed
+on host cores), and its plan-configuration parser."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert "workload" in d["config"]
+
+
+def test_plan_config_parser():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_cfg("chunked:2,2") == dict(schedule="chunked", Bu=2, Bv=2)
+    assert bench.parse_cfg("chunked:4,2:128") == dict(schedule="chunked", Bu=4, Bv=2, vis_per_chunk=128)
+    assert bench.parse_cfg("patch:2,2:64:384") == dict(schedule="patch", Bu=2, Bv=2, vis_per_chunk=64, threads=384)
