@@ -143,6 +143,18 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(policy_stream()));
   return v;
 }
+// A hint that brings bytes [p, p + n) into L2 ahead of their first use: bulk
+// prefetches (8 KB at most each) of the whole 16-byte units inside the range.
+// No registers are held and nothing waits for them.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t n) {
+  const uintptr_t s = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + n) & ~(uintptr_t)15;
+  for (uintptr_t q = s; q < e; q += 8192) {
+    const unsigned len = (unsigned)(e - q < 8192 ? e - q : 8192);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(len) : "memory");
+  }
+}
+
 // output visibilities (degridding): written once
 __device__ __forceinline__ void st_stream(float* p, float v) {
   asm volatile("st.global.L1::no_allocate.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy_stream()) : "memory");
@@ -231,51 +243,73 @@ __device__ __forceinline__ unsigned box_key(const int4 m, const TeamPos& t, cons
   return (unsigned)m.x + t.A + (wu ? (unsigned)g.nu : 0u) + (wv ? ((unsigned)g.nv << 16) : 0u);
 }
 
+// The raw words of one record's P values (2P words for FP32 pairs, P words
+// for 16-bit pairs), loaded apart from their conversion so that staging can
+// issue every load of a pass before it waits on any of them.
 template <int P>
-__device__ __forceinline__ void load_vis(const Args& a, long long k, float w, float2 (&val)[P]) {
+struct VisWords {
+  uint32_t w[2 * P];
+};
+
+template <int P>
+__device__ __forceinline__ void load_vis_words(const Args& a, long long k, VisWords<P>& q) {
   if (a.vis_fmt == FMT_F32) {
     const float2* src = (const float2*)a.vis + k * P;
     if constexpr (P % 2 == 0) {
 #pragma unroll
       for (int p = 0; p < P; p += 2) {
-        const float4 q = *(const float4*)(src + p);
-        val[p] = make_float2(q.x * w, q.y * w);
-        val[p + 1] = make_float2(q.z * w, q.w * w);
+        const uint4 t = *(const uint4*)(src + p);
+        q.w[2 * p] = t.x; q.w[2 * p + 1] = t.y; q.w[2 * p + 2] = t.z; q.w[2 * p + 3] = t.w;
       }
     } else {
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        const float2 q = src[p];
-        val[p] = make_float2(q.x * w, q.y * w);
+        const uint2 t = *(const uint2*)(src + p);
+        q.w[2 * p] = t.x; q.w[2 * p + 1] = t.y;
       }
     }
   } else {
-    // 16-bit pairs: P complex values = P 32-bit words
     const uint32_t* src = (const uint32_t*)a.vis + k * P;
-    uint32_t wds[P];
     if constexpr (P == 4) {
-      const uint4 q = *(const uint4*)src;
-      wds[0] = q.x; wds[1] = q.y; wds[2] = q.z; wds[3] = q.w;
+      const uint4 t = *(const uint4*)src;
+      q.w[0] = t.x; q.w[1] = t.y; q.w[2] = t.z; q.w[3] = t.w;
     } else if constexpr (P == 2) {
-      const uint2 q = *(const uint2*)src;
-      wds[0] = q.x; wds[1] = q.y;
+      const uint2 t = *(const uint2*)src;
+      q.w[0] = t.x; q.w[1] = t.y;
     } else {
 #pragma unroll
-      for (int p = 0; p < P; ++p) wds[p] = src[p];
+      for (int p = 0; p < P; ++p) q.w[p] = src[p];
     }
+  }
+}
+
+// w * V_p for the loaded words (16-bit pairs widened to FP32 first).
+template <int P>
+__device__ __forceinline__ void vis_values(const Args& a, const VisWords<P>& q, float w, float2 (&val)[P]) {
+  if (a.vis_fmt == FMT_F32) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) val[p] = make_float2(__uint_as_float(q.w[2 * p]) * w, __uint_as_float(q.w[2 * p + 1]) * w);
+  } else {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       float2 f;
       if (a.vis_fmt == FMT_BF16) {
-        __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&wds[p]);
+        __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.w[p]);
         f = __bfloat1622float2(b);
       } else {
-        __half2 hh = *reinterpret_cast<const __half2*>(&wds[p]);
+        __half2 hh = *reinterpret_cast<const __half2*>(&q.w[p]);
         f = __half22float2(hh);
       }
       val[p] = make_float2(f.x * w, f.y * w);
     }
   }
+}
+
+template <int P>
+__device__ __forceinline__ void load_vis(const Args& a, long long k, float w, float2 (&val)[P]) {
+  VisWords<P> q;
+  load_vis_words<P>(a, k, q);
+  vis_values<P>(a, q, w, val);
 }
 
 template <int B>
@@ -576,30 +610,43 @@ __device__ __forceinline__ void window_flush(bool need, unsigned key, float2 (&a
 
 // ---------------------------------------------------------------------------
 // Staging: batch b of a team's chunk goes into shared memory. Each team
-// thread loads records l, l+ts, ... of the batch (Sec. 4: "each work-item
-// loads one visibility").
+// thread stages records l, l+ts, ... of the batch (Sec. 4: "each work-item
+// loads one visibility"). A thread issues a record's three loads (position,
+// weight, values) together, before the index conversion, so it waits for one
+// memory latency per record rather than two dependent ones. Values are thus
+// loaded for every record in range, valid or not. (Two records per pass, all
+// six loads first, needs 112 registers instead of 80.)
+template <int BU, int BV, int P>
+__device__ __forceinline__ void stage_record(const Args& a, bool have, double2 x, float w, const VisWords<P>& q,
+                                             int4* meta, float2* vals) {
+  int4 m;
+  m.x = (int)kInvalid;
+  if (have && !make_meta<BU, BV>(a, x, m)) atomicAdd(a.skipped, 1ULL);
+  *meta = m;
+  if (m.x != (int)kInvalid) {
+    float2 val[P];
+    vis_values<P>(a, q, w, val);
+#pragma unroll
+    for (int p = 0; p < P; ++p) vals[p] = val[p];
+  }
+}
+
 template <int BU, int BV, int P, int RB = kRB>
 __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long long vend, int b, int l, int4* meta,
                                             float2* vals) {
   const Geometry& g = a.g;
+  const long long kb = vbeg + (long long)b * RB;
   for (int r = l; r < RB; r += g.ts) {
-    const long long k = vbeg + (long long)b * RB + r;
-    int4 m;
-    m.x = (int)kInvalid;
-    float2 val[P];
-    if (k < vend) {
-      if (make_meta<BU, BV>(a, a.uv[k], m)) {
-        const float w = a.weights ? a.weights[k] : 1.f;
-        load_vis<P>(a, k, w, val);
-      } else {
-        atomicAdd(a.skipped, 1ULL);
-      }
+    const bool h = kb + r < vend;
+    double2 x = make_double2(0.0, 0.0);
+    float w = 1.f;
+    VisWords<P> q;
+    if (h) {
+      x = a.uv[kb + r];
+      if (a.weights) w = a.weights[kb + r];
+      load_vis_words<P>(a, kb + r, q);
     }
-    meta[r] = m;
-    if (m.x != (int)kInvalid) {
-#pragma unroll
-      for (int p = 0; p < P; ++p) vals[r * P + p] = val[p];
-    }
+    stage_record<BU, BV, P>(a, h, x, w, q, meta + r, vals + r * P);
   }
 }
 
@@ -992,6 +1039,12 @@ __global__ void degrid_kernel(Args a) {
   const long long chunk = (long long)blockIdx.x * g.tpc + team;
   const long long vbeg = chunk * a.chunk_len;
   const long long vend = chunk < a.n_chunks ? min(vbeg + a.chunk_len, a.n_vis) : vbeg;
+  if (l == 0 && vend > vbeg) {
+    // the chunk's positions and weights go to L2 now, so that the staging of
+    // every batch after the first waits for L2 rather than HBM
+    prefetch_l2(a.uv + vbeg, (size_t)(vend - vbeg) * sizeof(double2));
+    if (a.weights) prefetch_l2(a.weights + vbeg, (size_t)(vend - vbeg) * sizeof(float));
+  }
   int4* const mt0 = meta + team * kRBD;
   int4* const mt1 = meta + (g.tpc + team) * kRBD;
   constexpr int QW = degrid_qw(P);
