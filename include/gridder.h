@@ -354,6 +354,22 @@ const char* grid_patch_static_last_error(void);
 /* Message of the last error on the calling thread ("" if none). */
 const char* grid_last_error(void);
 
+/* How the kernels for a Bu x Bv block and npol polarizations form the
+ * products t_u[i] t_v[j] V_p of one visibility (the Sec. 6 remark on the
+ * separable GCF), chosen at compile time per kernel as the form with the
+ * fewest multiplications:
+ *   GRID_TAPS_PRODUCT  (0): w_ij = t_u[i] t_v[j] first, then w_ij V_p;
+ *   GRID_TAPS_FACTOR_V (1): Y_jp = t_v[j] V_p first, then t_u[i] Y_jp;
+ *   GRID_TAPS_FACTOR_U (2): X_ip = t_u[i] V_p first, then t_v[j] X_ip.
+ * *form receives the form and *multiplies the multiplications per visibility
+ * per block, counted as in Sec. 6 (a real-by-complex product counts as one):
+ * Bu*Bv + Bu*Bv*npol, Bv*npol + Bu*Bv*npol or Bu*npol + Bu*Bv*npol. Either
+ * output may be null, not both. Host only (no device is touched). Returns
+ * GRID_OK, GRID_ERR_INVALID (bad sizes, both outputs null) or
+ * GRID_ERR_UNSUPPORTED (no kernel is built for the shape). */
+enum { GRID_TAPS_PRODUCT = 0, GRID_TAPS_FACTOR_V = 1, GRID_TAPS_FACTOR_U = 2 };
+int grid_tap_form(int Bu, int Bv, int npol, int* form, int* multiplies);
+
 /* Peak FP32 FMA lanes per SM per clock (128 on sm_103) and the SM count of the current device. */
 int grid_device_info(int* sm_count, int* fma_lanes_per_sm, int* max_clock_khz);
 

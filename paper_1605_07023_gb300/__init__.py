@@ -324,6 +324,17 @@ def device_info() -> dict:
     return dict(sm_count=sms.value, fma_lanes_per_sm=lanes.value, max_clock_khz=clk.value)
 
 
+TAP_FORMS = ("product", "factor_v", "factor_u")
+
+
+def tap_form(Bu: int, Bv: int, npol: int) -> tuple[str, int]:
+    """How the kernels for a Bu x Bv block form the tap products (Sec. 6 remark), and their
+    multiplications per visibility per block (grid_tap_form in the C ABI; host only)."""
+    form, mults = ctypes.c_int(), ctypes.c_int()
+    _lib.check(_lib.load().grid_tap_form(Bu, Bv, npol, ctypes.byref(form), ctypes.byref(mults)))
+    return TAP_FORMS[form.value], mults.value
+
+
 class BatchPlan:
     """Batched gridding of many grids in one persistent launch (grid_batch_* in the C ABI).
 

@@ -22,7 +22,7 @@ SCHED = {"chunked": 0, "patch": 1}
 
 EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped",
-           "grid_last_error", "grid_device_info", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
+           "grid_last_error", "grid_device_info", "grid_tap_form", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
            "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
            "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host", "grid_batch_create_ex",
            "grid_degrid_host_steps")
@@ -100,6 +100,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid_last_error.restype = ctypes.c_char_p
     lib.grid_device_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.grid_device_info.restype = i32
+    lib.grid_tap_form.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.grid_tap_form.restype = i32
     lib.grid_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, i32, i32, i32]
     lib.grid_batch_create.restype = i32
     lib.grid_batch_create_ex.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32, i32]

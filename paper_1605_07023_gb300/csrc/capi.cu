@@ -659,6 +659,21 @@ int grid_degrid_host_steps(grid_plan_t gp, grid_plan_t dp, int n_steps, const gr
   return GRID_OK;
 }
 
+int grid_tap_form(int Bu, int Bv, int npol, int* form, int* multiplies) {
+  if (!form && !multiplies) return fail(GRID_ERR_INVALID, "grid_tap_form: both outputs are null");
+  if (Bu < 1 || Bv < 1 || !(npol == 1 || npol == 2 || npol == 4))
+    return fail(GRID_ERR_INVALID, "grid_tap_form: Bu=%d Bv=%d npol=%d out of range", Bu, Bv, npol);
+  const KernelEntry* k = find_kernel(Bu, Bv, npol);
+  if (!k) return fail(GRID_ERR_UNSUPPORTED, "grid_tap_form: no kernel for Bu=%d Bv=%d npol=%d", Bu, Bv, npol);
+  // Sec. 6: B*B (or B*P) multiplies before the products, then one per (cell, polarization)
+  static_assert(TAP_PRODUCT == GRID_TAPS_PRODUCT && TAP_FACTOR_V == GRID_TAPS_FACTOR_V &&
+                TAP_FACTOR_U == GRID_TAPS_FACTOR_U, "tap form codes");
+  const int pre = k->form == TAP_PRODUCT ? Bu * Bv : (k->form == TAP_FACTOR_V ? Bv * npol : Bu * npol);
+  if (form) *form = k->form;
+  if (multiplies) *multiplies = pre + Bu * Bv * npol;
+  return GRID_OK;
+}
+
 int grid_device_info(int* sm_count, int* fma_lanes_per_sm, int* max_clock_khz) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -5,7 +5,7 @@
 namespace gbg {
 
 #define GB_ENTRY(BU, BV)                                                                                  \
-  {BU, BV, 1, (const void*)&grid_kernel<BU, BV, 1, false>, (const void*)&grid_kernel<BU, BV, 1, true>, \
+  {BU, BV, 1, TapForm<BU, BV, 1>::value, (const void*)&grid_kernel<BU, BV, 1, false>, (const void*)&grid_kernel<BU, BV, 1, true>, \
    (const void*)&degrid_kernel<BU, BV, 1>, &grid_smem_bytes<BU, BV, 1>, \
    &degrid_smem_bytes<BU, BV, 1>}
 

@@ -5,7 +5,7 @@
 namespace gbg {
 
 #define GB_ENTRY(BU, BV)                                                                                  \
-  {BU, BV, 2, (const void*)&grid_kernel<BU, BV, 2, false>, (const void*)&grid_kernel<BU, BV, 2, true>, \
+  {BU, BV, 2, TapForm<BU, BV, 2>::value, (const void*)&grid_kernel<BU, BV, 2, false>, (const void*)&grid_kernel<BU, BV, 2, true>, \
    (const void*)&degrid_kernel<BU, BV, 2>, &grid_smem_bytes<BU, BV, 2>, \
    &degrid_smem_bytes<BU, BV, 2>}
 

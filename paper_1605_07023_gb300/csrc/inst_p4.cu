@@ -5,7 +5,7 @@
 namespace gbg {
 
 #define GB_ENTRY(BU, BV)                                                                                  \
-  {BU, BV, 4, (const void*)&grid_kernel<BU, BV, 4, false>, (const void*)&grid_kernel<BU, BV, 4, true>, \
+  {BU, BV, 4, TapForm<BU, BV, 4>::value, (const void*)&grid_kernel<BU, BV, 4, false>, (const void*)&grid_kernel<BU, BV, 4, true>, \
    (const void*)&degrid_kernel<BU, BV, 4>, &grid_smem_bytes<BU, BV, 4>, \
    &degrid_smem_bytes<BU, BV, 4>}
 

@@ -1135,6 +1135,7 @@ __global__ void degrid_kernel(Args a) {
 // shared-memory layout functions.
 struct KernelEntry {
   int bu, bv, p;
+  int form;                   // TapForm<bu, bv, p>::value: how the kernels form the tap products
   const void* grid_fn;        // chunked schedule
   const void* grid_patch_fn;  // patch schedule
   const void* degrid_fn;
