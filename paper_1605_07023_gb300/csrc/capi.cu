@@ -666,8 +666,8 @@ int grid_tap_form(int Bu, int Bv, int npol, int* form, int* multiplies) {
   const KernelEntry* k = find_kernel(Bu, Bv, npol);
   if (!k) return fail(GRID_ERR_UNSUPPORTED, "grid_tap_form: no kernel for Bu=%d Bv=%d npol=%d", Bu, Bv, npol);
   // Sec. 6: B*B (or B*P) multiplies before the products, then one per (cell, polarization)
-  static_assert(TAP_PRODUCT == GRID_TAPS_PRODUCT && TAP_FACTOR_V == GRID_TAPS_FACTOR_V &&
-                TAP_FACTOR_U == GRID_TAPS_FACTOR_U, "tap form codes");
+  static_assert((int)TAP_PRODUCT == (int)GRID_TAPS_PRODUCT && (int)TAP_FACTOR_V == (int)GRID_TAPS_FACTOR_V &&
+                (int)TAP_FACTOR_U == (int)GRID_TAPS_FACTOR_U, "tap form codes");
   const int pre = k->form == TAP_PRODUCT ? Bu * Bv : (k->form == TAP_FACTOR_V ? Bv * npol : Bu * npol);
   if (form) *form = k->form;
   if (multiplies) *multiplies = pre + Bu * Bv * npol;
