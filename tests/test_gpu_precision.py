@@ -92,3 +92,29 @@ def test_degrid_with_16bit_taps(gb, prec):
     torch.cuda.synchronize()
     ref, _ = oracle.degrid(w.G, w.S, w.oversample, w.uv, g, tab_r)
     assert rel_l2(out.cpu().numpy()[:, 0], ref[:, 0]) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("npol,B", [(2, 2), (4, 2), (4, 1), (2, 3)])
+def test_precision_multi_polarization_weighted(gb, prec, npol, B):
+    """16-bit values of 2 and 4 polarizations (one 64- or 128-bit load per record), non-unit weights,
+    a ragged last chunk: FP32 accumulation against the oracle given the same rounded inputs."""
+    base = synth.scaled_down(synth.quad_pol(), 50_001)
+    rng = np.random.default_rng(40 + npol)
+    wts = rng.uniform(0.1, 3.0, base.n_vis).astype(np.float32)
+    vis = base.vis[:, :npol].copy()
+    tdt = torch.bfloat16 if prec == "bf16" else torch.float16
+    vis16 = torch.view_as_real(torch.from_numpy(vis)).to(tdt).contiguous()
+    table16 = host_table(base, prec)
+    plan = gb.Plan(base.G, base.S, base.oversample, npol, B=B, precision=prec)
+    g = torch.zeros((npol, base.G, base.G), dtype=torch.complex64, device="cuda")
+    gb.grid(plan, torch.from_numpy(base.uv).cuda(), vis16.cuda(), torch.from_numpy(wts).cuda(), table16, g)
+    torch.cuda.synchronize()
+    vis_r = vis16.float().numpy()
+    vis_r = (vis_r[..., 0] + 1j * vis_r[..., 1]).astype(np.complex128)
+    ref, sk = oracle.grid(base.G, base.S, base.oversample, base.uv, vis_r, wts,
+                          table16.float().cpu().numpy().astype(np.float64))
+    assert plan.skipped() == sk
+    got = g.cpu().numpy()
+    for p in range(npol):
+        assert rel_l2(got[p], ref[p]) <= 1e-5, p
