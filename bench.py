@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="auto", help="grid plan: auto | chunked:Bu,Bv[:vis_per_chunk[:threads]] | patch:Bu,Bv[:vis_per_chunk[:threads]]")
-    ap.add_argument("--degrid-config", default="auto")
+    ap.add_argument("--degrid-config", default="auto", help="degrid plan: auto | chunked:Bu,Bv[:L[:T]] | tile:Bu,Bv:0:T")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--vis", type=int, default=0, help="use only the first N visibilities (profiling runs)")
@@ -366,19 +366,19 @@ def main():
     g_tflops = useful_flops / (g_ms / 1e3) / 1e12
     d_tflops = useful_flops / (d_ms / 1e3) / 1e12
     pg_tflops = useful_flops / (p_g / 1e3) / 1e12
-    dominant = "grid" if g_ms >= d_ms else "degrid"
+    dominant = "grid" if g_ms >= d_ms else ("degrid_tile" if best_degrid["schedule"] == "tile" else "degrid")
     achieved = g_tflops if dominant == "grid" else d_tflops
 
     # DRAM bytes per launch from one ncu capture (profiles/traffic.json), used only while the
-    # kernel source is the one that was captured
+    # kernel's source file is the one that was captured
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath) and not args.vis:
         try:
-            rec = json.load(open(tpath))
-            src = open(os.path.join(ROOT, "paper_1605_07023_gb300", "csrc", "kernels.cuh"), "rb").read()
-            if hashlib.sha256(src).hexdigest()[:16] == rec.get("kernels_cuh_sha256_16"):
-                traffic = rec.get(dominant)
+            ent = json.load(open(tpath))["kernels"][dominant]
+            src = open(os.path.join(ROOT, "paper_1605_07023_gb300", "csrc", ent["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == ent["sha256_16"]:
+                traffic = ent["bytes"]
         except Exception:
             traffic = None
 

@@ -76,7 +76,16 @@ enum {
    * halo in shared memory. Register flushes that land there use shared
    * atomics, and flushes that land outside it go to global memory. The patch
    * reaches the grid once per work item, with coalesced vector atomics. */
-  GRID_SCHED_PATCH = 1
+  GRID_SCHED_PATCH = 1,
+  /* Gridding as GRID_SCHED_CHUNKED. Degridding by tile gather: each warp
+   * takes 32 consecutive visibilities, copies the bounding box of their
+   * footprints (up to (S+13) x (S+13) cells per polarization) from the grid
+   * into shared memory, and each lane sums its own visibility's footprint
+   * from there, with no reduction between threads (rows first, the separable
+   * form of the Sec. 6 remark). A group whose box is larger reads the grid
+   * directly. The same results as the chunked degridder up to FP32 rounding.
+   * Built for odd S <= 15; threads must be a multiple of 32. */
+  GRID_SCHED_TILE = 2
 };
 
 typedef struct {

@@ -26,6 +26,7 @@ DEGRID_LENGTHS = (64, 128, 256)
 # Target CTA sizes (threads per CTA, rounded down to whole teams). Smaller CTAs let more of the
 # register-limited teams be resident per SM.
 CTA_THREADS = (128, 256)
+TILE_THREADS = (32, 64, 128)   # tile-schedule degridding: warps per CTA x 32
 
 
 def _cache_path() -> str:
@@ -76,6 +77,10 @@ def _candidates(kind: str):
             for L in DEGRID_LENGTHS:
                 for T in CTA_THREADS:
                     yield dict(schedule="chunked", Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
+    if kind == "degrid":
+        # the tile schedule does not use Bu, Bv or the chunk length for degridding
+        for T in TILE_THREADS:
+            yield dict(schedule="tile", Bu=2, Bv=2, vis_per_chunk=0, threads=T)
 
 
 def _time(fn, reps: int) -> float:

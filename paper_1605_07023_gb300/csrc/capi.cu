@@ -24,6 +24,10 @@ struct grid_plan_s {
   size_t smem_degrid;
   int occ_grid;         // resident gridding CTAs per SM (patch schedule)
   int warp_sync;        // team size divides 32: teams synchronise per warp
+  const TileKernel* tile;  // tile schedule: the degridding kernel, its CTA size and shared memory
+  int tile_threads;
+  size_t tile_smem;
+  int occ_tile;            // resident tile-degridding CTAs per SM
   unsigned long long* d_skipped;
   PatchScratch ps;
   long long ps_chunks_cap;  // chunk capacity of the patch scratch
@@ -182,7 +186,10 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   if (d.npol != 1 && d.npol != 2 && d.npol != 4) return fail(GRID_ERR_INVALID, "npol=%d: must be 1, 2 or 4", d.npol);
   if (d.Bu < 1 || d.Bu > 8 || d.Bv < 1 || d.Bv > 8) return fail(GRID_ERR_INVALID, "B=(%d,%d): must be 1..8", d.Bu, d.Bv);
   if (d.precision < GRID_PREC_F32 || d.precision > GRID_PREC_F16) return fail(GRID_ERR_INVALID, "precision=%d", d.precision);
-  if (d.schedule != GRID_SCHED_CHUNKED && d.schedule != GRID_SCHED_PATCH) return fail(GRID_ERR_INVALID, "schedule=%d", d.schedule);
+  if (d.schedule != GRID_SCHED_CHUNKED && d.schedule != GRID_SCHED_PATCH && d.schedule != GRID_SCHED_TILE)
+    return fail(GRID_ERR_INVALID, "schedule=%d", d.schedule);
+  if (d.threads % 32 != 0 && d.schedule == GRID_SCHED_TILE)
+    return fail(GRID_ERR_INVALID, "threads=%d: the tile schedule needs whole warps", d.threads);
   if (d.vis_per_chunk < 0 || d.vis_per_chunk > (1 << 20)) return fail(GRID_ERR_INVALID, "vis_per_chunk=%d", d.vis_per_chunk);
   if (d.threads < 0 || d.threads > 1024) return fail(GRID_ERR_INVALID, "threads=%d", d.threads);
   const KernelEntry* k = find_kernel(d.Bu, d.Bv, d.npol);
@@ -255,7 +262,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     s.win = win;
     s.max_chunks = 256;
   }
-  if (d.schedule == GRID_SCHED_CHUNKED) {
+  if (d.schedule != GRID_SCHED_PATCH) {
     // small teams (tiny S and B) put many teams in a CTA: shrink the CTA until
     // its staging buffers fit
     while (g.tpc > 1 && (k->grid_smem(g, g.tpc * g.ts, 0) + fa_g.sharedSizeBytes > smem_max ||
@@ -279,6 +286,28 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occ_grid, pl->grid_fn, pl->threads, pl->smem_grid);
     if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"); }
     if (pl->occ_grid < 1) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "gridding kernel cannot be resident with this shape"); }
+  }
+  if (d.schedule == GRID_SCHED_TILE) {
+    const TileKernel* t = find_tile_kernel(d.S, d.npol);
+    if (!t) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "tile schedule: no kernel for S=%d npol=%d (odd S <= 15)", d.S, d.npol); }
+    cudaFuncAttributes fa_t;
+    e = cudaFuncGetAttributes(&fa_t, t->fn);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncGetAttributes (tile)"); }
+    int warps = (d.threads > 0 ? d.threads : 256) / 32;
+    if (warps * 32 > fa_t.maxThreadsPerBlock) warps = fa_t.maxThreadsPerBlock / 32;
+    while (warps > 1 && tile_smem_bytes(*t, g.O, warps) + fa_t.sharedSizeBytes > smem_max) --warps;
+    if (warps < 1 || tile_smem_bytes(*t, g.O, warps) + fa_t.sharedSizeBytes > smem_max) {
+      delete pl;
+      return fail(GRID_ERR_UNSUPPORTED, "tile schedule: one warp's tile does not fit in shared memory");
+    }
+    e = cudaFuncSetAttribute(t->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_t.sharedSizeBytes));
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute (tile)"); }
+    pl->tile = t;
+    pl->tile_threads = warps * 32;
+    pl->tile_smem = tile_smem_bytes(*t, g.O, warps);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pl->occ_tile, t->fn, pl->tile_threads, pl->tile_smem);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor (tile)"); }
+    if (pl->occ_tile < 1) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "tile degridding kernel cannot be resident"); }
   }
   e = cudaMalloc(&pl->d_skipped, sizeof(unsigned long long));
   if (e != cudaSuccess) { delete pl; return fail(GRID_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
@@ -334,7 +363,7 @@ int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const
   a.table = kernel_table;
   a.grid = (float2*)grid_out;
   cudaError_t e;
-  if (pl->desc.schedule == GRID_SCHED_CHUNKED) {
+  if (pl->desc.schedule != GRID_SCHED_PATCH) {
     const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
     void* args[] = {&a};
     e = cudaLaunchKernel(pl->grid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_grid, stream);
@@ -384,9 +413,19 @@ int degrid_weighted(grid_plan_t pl, int64_t n_vis, const double* uv, const void*
   a.table = kernel_table;
   a.grid = (float2*)grid_in;
   a.vis_out = (float2*)vis;
-  const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchKernel(pl->k->degrid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_degrid, stream);
+  cudaError_t e;
+  if (pl->tile) {
+    // persistent warps, one group of 32 visibilities at a time: one wave of resident CTAs
+    const long long groups = (n_vis + 31) / 32, wpc = pl->tile_threads / 32;
+    long long blocks = (groups + wpc - 1) / wpc;
+    if (blocks > (long long)pl->sm_count * pl->occ_tile) blocks = (long long)pl->sm_count * pl->occ_tile;
+    e = cudaLaunchKernel(pl->tile->fn, dim3((unsigned)blocks), dim3(pl->tile_threads), args, pl->tile_smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "degrid (tile) kernel launch");
+    return GRID_OK;
+  }
+  const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
+  e = cudaLaunchKernel(pl->k->degrid_fn, dim3((unsigned)blocks), dim3(pl->threads), args, pl->smem_degrid, stream);
   if (e != cudaSuccess) return cuda_fail(e, "degrid kernel launch");
   return GRID_OK;
 }

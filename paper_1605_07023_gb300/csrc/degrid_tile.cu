@@ -1,0 +1,187 @@
+// Degridding by tile gather: a second schedule for the adjoint of gridding.
+//
+// The sliding-window degridder mirrors the gridder: each thread keeps one
+// block of grid values in registers and a team reduces its partial sums
+// through shared memory for every visibility. Here each warp instead takes
+// 32 consecutive visibilities (one per lane). Consecutive visibilities of a
+// baseline lie close together on the grid (Sec. 2.2: the footprints of a
+// track almost entirely overlap), so the warp copies the bounding box of their
+// 32 footprints into a shared-memory tile once. Then every lane forms its own
+// visibility's P sums over the S x S footprint from the tile, with no
+// reduction between threads:
+//   s_p = sum_j t_v[j] * sum_i t_u[i] * g[p][y0 + j][x0 + i]
+// (the separable form of the Sec. 6 remark, rows first). A group whose box is
+// larger than the tile (fast tracks, unordered input) reads its footprints
+// from global memory instead, with the same arithmetic. (Splitting such a
+// group into two halves with a smaller tile measured slower.) Warps are
+// persistent and load the next group's positions one group ahead.
+//
+// The index rule, validity, skipped count and output layout are those of the
+// sliding-window degridder.
+#include "kernels.cuh"
+#include "internal.h"
+
+namespace gbg {
+namespace {
+
+// The smallest row stride >= w (in cells) that is odd mod 16 and not +-1 mod 16.
+constexpr int spread_stride(int w) {
+  return (w % 2 == 1 && w % 16 != 1 && w % 16 != 15) ? w : spread_stride(w + 1);
+}
+
+template <int S, int P>
+struct TileShape {
+  // Tile side in cells: the box of 32 consecutive visibilities on a baseline
+  // track fits unless the track is fast (a larger tile measured faster than
+  // S + 9, whose misses cost more than the lost occupancy).
+  static constexpr int TW = S + 13;
+  // Row stride in cells. A cell is two 4-byte banks, so cell (row, col) starts
+  // at bank pair (RS*row + col) mod 16. With RS odd and not +-1 mod 16, lanes
+  // whose footprints are one cell apart along a diagonal read different banks
+  // (a stride of TW + 1 = 1 mod 16 made every such pair collide).
+  static constexpr int RS = spread_stride(TW);
+  static constexpr int PS = TW * RS;    // plane stride in cells
+  static constexpr int CELLS = P * PS;  // complex cells per warp
+};
+
+// s_p for one visibility whose footprint starts at base (cell (x0, y0) of
+// plane 0), with rows RSTRIDE and planes PSTRIDE cells apart.
+template <int S, int P, typename Ptr, typename Stride>
+__device__ __forceinline__ void footprint_dot(Ptr base, Stride rstride, Stride pstride, const float (&tu)[S],
+                                              const float (&tv)[S], float2 (&s)[P]) {
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const Ptr row = base + (Stride)p * pstride + (Stride)j * rstride;
+      float2 r = __fmul2_rn(splat(tu[0]), row[0]);
+#pragma unroll
+      for (int i = 1; i < S; ++i) r = __ffma2_rn(splat(tu[i]), row[i], r);
+      s[p] = j == 0 ? __fmul2_rn(splat(tv[0]), r) : __ffma2_rn(splat(tv[j]), r, s[p]);
+    }
+  }
+}
+
+// An 8-byte global-to-shared copy that does not wait for its data
+// (cp.async); copy_async_wait_all() waits for all of the thread's copies.
+__device__ __forceinline__ void copy_async8(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The direct path for a group whose box does not fit the tile: kept out
+// of line so that it adds no registers to the tile path.
+template <int S, int P>
+__device__ __noinline__ void footprint_dot_global(const float2* base, int G, const float (&tu)[S],
+                                                  const float (&tv)[S], float2 (&s)[P]) {
+  footprint_dot<S, P>(base, (size_t)G, (size_t)G * G, tu, tv, s);
+}
+
+template <int S, int P>
+__global__ void degrid_tile_kernel(Args a) {
+  using T = TileShape<S, P>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Geometry& g = a.g;
+  float* tab = (float*)smem;
+  const int ntab = g.O * S;
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = load_tap(a.table, a.tab_fmt, i);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* tile = (float2*)(smem + align16((size_t)ntab * 4)) + (size_t)warp * T::CELLS;
+  __syncthreads();
+
+  const int G = g.G;
+  const size_t GG = (size_t)G * G;
+  const long long n_groups = (a.n_vis + 31) >> 5;
+  const long long stride = (long long)gridDim.x * (blockDim.x >> 5);
+  // Persistent warps: the position of the next group's visibility is loaded
+  // one group ahead, so its memory latency overlaps the current group.
+  long long c = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+  double2 xn = make_double2(0.0, 0.0);
+  if (c < n_groups && c * 32 + lane < a.n_vis) xn = ld_stream(a.uv + c * 32 + lane);
+  for (; c < n_groups; c += stride) {
+    const long long k = c * 32 + lane;
+    const double2 x = xn;
+    if (c + stride < n_groups && (c + stride) * 32 + lane < a.n_vis) xn = ld_stream(a.uv + (c + stride) * 32 + lane);
+    int x0 = 0, y0 = 0, ru = 0, rv = 0;
+    bool ok = false;
+    if (k < a.n_vis) {
+      int Cu, Cv;
+      ok = fine_cell(x.x, g.log2O, G >> 1, Cu, ru);
+      ok = fine_cell(x.y, g.log2O, G >> 1, Cv, rv) && ok;
+      x0 = Cu - g.h;
+      y0 = Cv - g.h;
+      ok = ok && x0 >= 0 && x0 + S <= G && y0 >= 0 && y0 + S <= G;
+      if (!ok) atomicAdd(a.skipped, 1ULL);
+    }
+    float2 s[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) s[p] = make_float2(0.f, 0.f);
+    float tu[S], tv[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      tu[i] = tab[ru * S + i];
+      tv[i] = tab[rv * S + i];
+    }
+    const int xmin = __reduce_min_sync(0xFFFFFFFFu, ok ? x0 : 0x7FFFFFFF);
+    const int ymin = __reduce_min_sync(0xFFFFFFFFu, ok ? y0 : 0x7FFFFFFF);
+    const int xmax = __reduce_max_sync(0xFFFFFFFFu, ok ? x0 : -1);
+    const int ymax = __reduce_max_sync(0xFFFFFFFFu, ok ? y0 : -1);
+    if (xmax >= 0) {
+      const int sx = xmax - xmin + S, sy = ymax - ymin + S;
+      if (sx <= T::TW && sy <= T::TW) {
+        // Copy the box with asynchronous 8-byte copies (all of a lane's copies
+        // in flight at once): rows of sx cells, lanes spread over 32 / sx rows
+        // at a time. The box lies inside the grid (a union of valid footprints).
+        const int rpp = 32 / sx;
+        const int lr = lane / sx, col = lane - lr * sx;
+        if (lr < rpp) {
+          int p = 0, row = lr;
+          for (int r = lr; r < P * sy; r += rpp) {
+            while (row >= sy) { row -= sy; ++p; }
+            copy_async8(tile + p * T::PS + row * T::RS + col,
+                        a.grid + (size_t)p * GG + (size_t)(ymin + row) * G + (xmin + col));
+            row += rpp;
+          }
+        }
+        copy_async_wait_all();
+        __syncwarp();
+        if (ok) footprint_dot<S, P>((const float2*)tile + (y0 - ymin) * T::RS + (x0 - xmin), T::RS, T::PS, tu, tv, s);
+        __syncwarp();  // the tile is refilled for the next group
+      } else if (ok) {
+        footprint_dot_global<S, P>((const float2*)a.grid + (size_t)y0 * G + x0, G, tu, tv, s);
+      }
+    }
+    if (k < a.n_vis) {
+      const float w = (a.weights && ok) ? a.weights[k] : 1.f;
+      float2* out = a.vis_out + k * P;
+#pragma unroll
+      for (int p = 0; p < P; ++p) __stcs(out + p, make_float2(s[p].x * w, s[p].y * w));
+    }
+  }
+}
+
+template <int S, int P>
+TileKernel tile_entry() {
+  return TileKernel{S, P, (const void*)&degrid_tile_kernel<S, P>, TileShape<S, P>::CELLS};
+}
+
+#define GB_TILE_ROW(P) \
+  tile_entry<1, P>(), tile_entry<3, P>(), tile_entry<5, P>(), tile_entry<7, P>(), tile_entry<9, P>(), \
+      tile_entry<11, P>(), tile_entry<13, P>(), tile_entry<15, P>()
+
+const TileKernel kTileKernels[] = {GB_TILE_ROW(1), GB_TILE_ROW(2), GB_TILE_ROW(4)};
+
+}  // namespace
+
+const TileKernel* find_tile_kernel(int S, int P) {
+  for (const TileKernel& t : kTileKernels)
+    if (t.S == S && t.P == P) return &t;
+  return nullptr;
+}
+
+size_t tile_smem_bytes(const TileKernel& t, int O, int warps) {
+  return align16((size_t)O * t.S * 4) + (size_t)warps * t.cells * sizeof(float2);
+}
+
+}  // namespace gbg

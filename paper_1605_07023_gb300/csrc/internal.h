@@ -31,6 +31,15 @@ const KernelEntry* kernels_p1(int* n);
 const KernelEntry* kernels_p2(int* n);
 const KernelEntry* kernels_p4(int* n);
 
+// Tile-gather degridding (degrid_tile.cu), one kernel per (S, P).
+struct TileKernel {
+  int S, P;
+  const void* fn;
+  int cells;  // complex cells of one warp's tile
+};
+const TileKernel* find_tile_kernel(int S, int P);
+size_t tile_smem_bytes(const TileKernel& t, int O, int warps);
+
 cudaError_t launch_kb_table(int S, int O, double beta, int fmt, void* out, cudaStream_t st);
 cudaError_t launch_indices(const Args& a, int32_t* cell, int32_t* sub, cudaStream_t st);
 cudaError_t launch_patch_binning(const Args& a, const PatchScratch& ps, cudaStream_t st);
