@@ -41,7 +41,7 @@ def rel_l2(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
-@pytest.mark.parametrize("schedule", ["chunked", "patch"])
+@pytest.mark.parametrize("schedule", ["chunked", "patch", "tile"])
 def test_grid_backward_is_weighted_adjoint(gb, schedule):
     from paper_1605_07023_gb300.autograd import grid_op
     w = synth.scaled_down(synth.quad_pol(), 60_000)

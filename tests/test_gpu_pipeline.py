@@ -33,15 +33,16 @@ def pinned(x):
     return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
 
 
+@pytest.mark.parametrize("dsched", ["chunked", "tile"])
 @pytest.mark.parametrize("weighted", [True, False])
-def test_pipelined_pass_matches_oracle(gb, weighted):
+def test_pipelined_pass_matches_oracle(gb, weighted, dsched):
     w = synth.scaled_down(synth.quad_pol(), 300_007)
     rng = np.random.default_rng(21)
     wt = rng.uniform(0.2, 2.0, w.n_vis).astype(np.float32) if weighted else None
     t64 = oracle.kb_table(w.S, w.oversample, w.beta).astype(np.float32).astype(np.float64)
     table = torch.from_numpy(t64.astype(np.float32)).cuda()
     gplan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=2, vis_per_chunk=128, threads=128)
-    dplan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=2)
+    dplan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=2, schedule=dsched)
     h_uv, h_vis = pinned(w.uv), pinned(w.vis)
     h_wt = None if wt is None else pinned(wt)
     h_out = torch.empty((w.n_vis, w.npol), dtype=torch.complex64).pin_memory()
@@ -79,14 +80,15 @@ def test_pipelined_pass_empty_and_mismatch(gb):
                             torch.empty((100, 1), dtype=torch.complex64).pin_memory())
 
 
+@pytest.mark.parametrize("dsched", ["chunked", "tile"])
 @pytest.mark.parametrize("weighted", [True, False])
-def test_pipelined_steps_match_oracle(gb, weighted):
+def test_pipelined_steps_match_oracle(gb, weighted, dsched):
     base = synth.scaled_down(synth.quad_pol(), 120_001)
     rng = np.random.default_rng(22)
     t64 = oracle.kb_table(base.S, base.oversample, base.beta).astype(np.float32).astype(np.float64)
     table = torch.from_numpy(t64.astype(np.float32)).cuda()
     gplan = gb.Plan(base.G, base.S, base.oversample, base.npol, B=2, vis_per_chunk=128, threads=128)
-    dplan = gb.Plan(base.G, base.S, base.oversample, base.npol, B=2)
+    dplan = gb.Plan(base.G, base.S, base.oversample, base.npol, B=2, schedule=dsched, threads=32 if dsched == "tile" else 0)
     steps, want = [], []
     for s in range(3):
         # each step: the same tracks with its own values and weights
