@@ -35,9 +35,13 @@ def _cache_path() -> str:
 
 
 def _key(kind: str, G: int, S: int, O: int, P: int, precision: str) -> str:
+    """Cache key: device, problem, and the candidate lists (a result tuned over other candidates,
+    for example before a schedule existed, is not reused)."""
+    import hashlib
     import torch
     name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
-    return f"{name}|{kind}|G{G}|S{S}|O{O}|P{P}|{precision}"
+    cands = repr((BLOCK_CANDIDATES, CHUNKED_LENGTHS, PATCH_LENGTHS, DEGRID_LENGTHS, CTA_THREADS, TILE_THREADS))
+    return f"{name}|{kind}|G{G}|S{S}|O{O}|P{P}|{precision}|{hashlib.sha256(cands.encode()).hexdigest()[:8]}"
 
 
 def load_cache() -> dict:
