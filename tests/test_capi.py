@@ -88,3 +88,17 @@ def test_newer_entry_points_reject_bad_arguments(lib):
     assert lib.grid_batch_create_ex(ctypes.byref(h), 1024, 8, 1, 2, 2, 4, 2, 99, 15, 0, 0, 0) == INV
     assert lib.grid_batch_create_ex(ctypes.byref(h), 1024, 8, 1, 2, 2, 8, 8, 13, 15, 0, 0, 0) == _lib.GRID_ERR_UNSUPPORTED
     assert not h.value
+
+
+def test_schedule_and_tile_threads_checked_on_the_host(lib):
+    """Unknown schedules, and a tile-schedule CTA size that is not whole warps, are rejected before
+    any device call."""
+    from paper_1605_07023_gb300 import _lib
+    h = ctypes.c_void_p()
+    for sched, threads in [(3, 0), (-1, 0), (_lib.SCHED["tile"], 48), (_lib.SCHED["tile"], 100)]:
+        d = _lib.GridPlanDesc()
+        lib.grid_plan_desc_init(ctypes.byref(d), 256, 7, 8, 4, 2)
+        d.schedule = sched
+        d.threads = threads
+        assert lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == _lib.GRID_ERR_INVALID, (sched, threads)
+        assert not h.value
