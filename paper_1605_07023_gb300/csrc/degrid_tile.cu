@@ -24,9 +24,9 @@
 namespace gbg {
 namespace {
 
-// The smallest row stride >= w (in cells) that is odd mod 16 and not +-1 mod 16.
+// The smallest even row stride >= w cells that is 6 or 10 mod 16.
 constexpr int spread_stride(int w) {
-  return (w % 2 == 1 && w % 16 != 1 && w % 16 != 15) ? w : spread_stride(w + 1);
+  return (w % 16 == 6 || w % 16 == 10) ? w : spread_stride(w + 1);
 }
 
 template <int S, int P>
@@ -35,10 +35,12 @@ struct TileShape {
   // track fits unless the track is fast (a larger tile measured faster than
   // S + 9, whose misses cost more than the lost occupancy).
   static constexpr int TW = S + 13;
-  // Row stride in cells. A cell is two 4-byte banks, so cell (row, col) starts
-  // at bank pair (RS*row + col) mod 16. With RS odd and not +-1 mod 16, lanes
-  // whose footprints are one cell apart along a diagonal read different banks
-  // (a stride of TW + 1 = 1 mod 16 made every such pair collide).
+  // Row stride in cells. It is even, so that rows start on 16-byte boundaries
+  // (the box is copied in 16-byte pieces). A cell is two 4-byte banks, so cell
+  // (row, col) starts at bank pair (RS*row + col) mod 16; with RS = 6 or 10
+  // mod 16, lanes whose footprints are a cell or two apart in any direction
+  // read different banks (a stride of TW + 1 = 1 mod 16 made every pair one
+  // cell apart along a diagonal collide).
   static constexpr int RS = spread_stride(TW);
   static constexpr int PS = TW * RS;    // plane stride in cells
   static constexpr int CELLS = P * PS;  // complex cells per warp
@@ -62,11 +64,12 @@ __device__ __forceinline__ void footprint_dot(Ptr base, Stride rstride, Stride p
   }
 }
 
-// An 8-byte global-to-shared copy that does not wait for its data
-// (cp.async); copy_async_wait_all() waits for all of the thread's copies.
-__device__ __forceinline__ void copy_async8(float2* dst, const float2* src) {
+// A 16-byte global-to-shared copy (two cells) that bypasses L1 and does not
+// wait for its data (cp.async.cg); both addresses are 16-byte aligned.
+// copy_async_wait_all() waits for all of the thread's copies.
+__device__ __forceinline__ void copy_async16(float2* dst, const float2* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void copy_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -128,25 +131,30 @@ __global__ void degrid_tile_kernel(Args a) {
     const int xmax = __reduce_max_sync(0xFFFFFFFFu, ok ? x0 : -1);
     const int ymax = __reduce_max_sync(0xFFFFFFFFu, ok ? y0 : -1);
     if (xmax >= 0) {
-      const int sx = xmax - xmin + S, sy = ymax - ymin + S;
-      if (sx <= T::TW && sy <= T::TW) {
-        // Copy the box with asynchronous 8-byte copies (all of a lane's copies
-        // in flight at once): rows of sx cells, lanes spread over 32 / sx rows
-        // at a time. The box lies inside the grid (a union of valid footprints).
-        const int rpp = 32 / sx;
-        const int lr = lane / sx, col = lane - lr * sx;
+      // The box starts at an even column, so that each row is whole 16-byte
+      // cell pairs (G is even and the grid 16-byte aligned); it lies inside
+      // the grid (a union of valid footprints, widened by at most one cell at
+      // each end of a row; the right end is checked).
+      const int xe = xmin & ~1;                    // first column of the copy
+      const int npair = (xmax + S - xe + 1) >> 1;  // cell pairs per row
+      const int sy = ymax - ymin + S;
+      if (2 * npair <= T::TW && sy <= T::TW && xe + 2 * npair <= G) {
+        // Copy with asynchronous 16-byte copies, all of a lane's copies in
+        // flight at once: lanes spread over 32 / npair rows at a time.
+        const int rpp = 32 / npair;
+        const int lr = lane / npair, pc = lane - lr * npair;
         if (lr < rpp) {
           int p = 0, row = lr;
           for (int r = lr; r < P * sy; r += rpp) {
             while (row >= sy) { row -= sy; ++p; }
-            copy_async8(tile + p * T::PS + row * T::RS + col,
-                        a.grid + (size_t)p * GG + (size_t)(ymin + row) * G + (xmin + col));
+            copy_async16(tile + p * T::PS + row * T::RS + 2 * pc,
+                         a.grid + (size_t)p * GG + (size_t)(ymin + row) * G + (xe + 2 * pc));
             row += rpp;
           }
         }
         copy_async_wait_all();
         __syncwarp();
-        if (ok) footprint_dot<S, P>((const float2*)tile + (y0 - ymin) * T::RS + (x0 - xmin), T::RS, T::PS, tu, tv, s);
+        if (ok) footprint_dot<S, P>((const float2*)tile + (y0 - ymin) * T::RS + (x0 - xe), T::RS, T::PS, tu, tv, s);
         __syncwarp();  // the tile is refilled for the next group
       } else if (ok) {
         footprint_dot_global<S, P>((const float2*)a.grid + (size_t)y0 * G + x0, G, tu, tv, s);
