@@ -643,6 +643,11 @@ __device__ __forceinline__ void stage_batch(const Args& a, long long vbeg, long 
       if (a.weights) w = a.weights[kb + r];
       load_vis_words<P>(a, kb + r, q);
     }
+    if (kb + RB + r < vend) {
+      // the record this thread stages next batch goes to L1 meanwhile
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.uv + kb + RB + r));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"((const char*)a.vis + (kb + RB + r) * (long long)P * (a.vis_fmt == FMT_F32 ? 8 : 4)));
+    }
     stage_record<BU, BV, P>(a, h, x, w, q, meta + r, vals + r * P);
   }
 }
