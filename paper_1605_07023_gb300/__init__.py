@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import GridderError, PREC, SCHED
 
 __all__ = ["Plan", "BatchPlan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "degrid_weighted", "grid_make_kernel_table",
-           "grid_compute_indices", "device_info", "GridderError"]
+           "grid_compute_indices", "device_info", "tap_form", "GridderError"]
 
 
 def _torch():
@@ -52,7 +52,12 @@ def _dptr(t, name: str, dtype=None, ndim=None) -> int:
 
 
 class Plan:
-    """Owns one grid_plan_t (destroyed on close() or garbage collection)."""
+    """Owns one grid_plan_t (destroyed on close() or garbage collection).
+
+    schedule: "chunked" (fixed visibilities per team, global flushes), "patch" (chunks binned by
+    grid patch, flushes into a shared-memory window), or "tile" (grids as "chunked"; degrids by
+    tile gather, one warp per 32 visibilities, threads a multiple of 32).
+    """
 
     def __init__(self, G: int, S: int, oversample: int, npol: int, B: int = 1, Bu: int | None = None,
                  Bv: int | None = None, vis_per_chunk: int = 0, threads: int = 0, precision: str = "f32",
