@@ -55,3 +55,21 @@ def test_efficiency_convention_reproduces_the_papers_numbers():
     assert g["uncoarsened_lo_pct"] - 0.5 <= plain * 100 <= g["uncoarsened_hi_pct"] + 0.5
     # the bench's GB300 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz
     assert abs(bench.fma_peak_tflops(152, 2070.0) - 80.54784) < 1e-6
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the driver launches N>1 (torchrun, two ranks): rank 0 alone times the oracle and
+    prints one line; the other rank exits 0 without work."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+           "--steps", "1", "--warmup", "0"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
