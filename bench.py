@@ -269,7 +269,8 @@ def measure_compression(gb, autotune, torch, dev, cfg_grid, cfg_degrid, steps, w
 
 
 def parse_cfg(s):
-    """'chunked:Bu,Bv[:L[:T]]' (L visibilities per chunk, T threads per CTA) -> plan config dict."""
+    """'schedule:Bu,Bv[:L[:T[:bin_u,bin_v]]]' (L visibilities per chunk, T threads per CTA, bin sides in
+    cells for the lazy schedule) -> plan config dict."""
     parts = s.split(":")
     bu, bv = (int(x) for x in parts[1].split(","))
     cfg = dict(schedule=parts[0], Bu=bu, Bv=bv)
@@ -277,6 +278,8 @@ def parse_cfg(s):
         cfg["vis_per_chunk"] = int(parts[2])
     if len(parts) > 3:
         cfg["threads"] = int(parts[3])
+    if len(parts) > 4:
+        cfg["bin_u"], cfg["bin_v"] = (int(x) for x in parts[4].split(","))
     return cfg
 
 

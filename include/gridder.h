@@ -85,7 +85,21 @@ enum {
    * form of the Sec. 6 remark). A group whose box is larger reads the grid
    * directly. The same results as the chunked degridder up to FP32 rounding.
    * Built for odd S <= 15; threads must be a multiple of 32. */
-  GRID_SCHED_TILE = 2
+  GRID_SCHED_TILE = 2,
+  /* Gridding with the Sec. 4 chunks and a wider bin than Sec. 3 needs
+   * (bin_u x bin_v cells, multiples of Bu and Bv, at most 32 threads per
+   * team). A thread still owns the blocks congruent to its position modulo
+   * the bin (Sec. 3), but the team's box around the footprint moves only
+   * when the footprint leaves it, and then by the fewest blocks. Paths that
+   * turn back inside the slack flush nothing; the cost is padding (more
+   * zero taps per visibility). With the paper's bin this is the paper's box
+   * rule. Built for (Bu, Bv) = (2,1) (2,2) (4,1) (4,2) (2,4) (8,1) at npol 4;
+   * (2,2) (4,2) (2,4) (4,4) (8,2) (2,8) at npol 2; those and (8,4) (4,8) (8,8)
+   * at npol 1. Threads a multiple of 32.
+   * Degridding with such a plan uses the chunked degridder on the paper's
+   * bin for the same (Bu, Bv), or for 2 x 2 blocks where no chunked kernel
+   * is built for (Bu, Bv). */
+  GRID_SCHED_LAZY = 3
 };
 
 typedef struct {
@@ -99,6 +113,10 @@ typedef struct {
   int precision;    /* GRID_PREC_* */
   int schedule;     /* GRID_SCHED_* */
   int patch;        /* GRID_SCHED_PATCH: patch side in cells; 0 = default */
+  int bin_u, bin_v; /* GRID_SCHED_LAZY: bin sides in cells (multiples of Bu, Bv, at least
+                       roundup(S + B - 1, B)); 0 = the paper's bin, one block wider along each
+                       axis where it leaves a footprint less than a block of room (u first), as
+                       long as the team stays within 32 threads */
 } grid_plan_desc;
 
 /* Fill `desc` with the defaults for the given problem and coarsening B (Bu = Bv = B). */
@@ -179,6 +197,18 @@ int grid_compute_indices(grid_plan_t plan, int64_t n_vis, const double* uv, int3
  * device counter. reset != 0 zeroes the counter afterwards.
  */
 int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
+
+/*
+ * Status flags of the plan's gridding calls since it was created or last
+ * reset (host call; synchronises with the device word). No passage of the
+ * paper defines it: it reports the lazy-box gridder's bounded waits.
+ *   bit 0 (GRID_STATUS_COPY_TIMEOUT): a bulk copy of a batch of records into
+ *   shared memory did not complete within the kernel's poll limit. The team
+ *   then skipped the rest of its chunk, so the grid is incomplete.
+ * reset != 0 zeroes the flags afterwards. flags must not be NULL.
+ */
+enum { GRID_STATUS_COPY_TIMEOUT = 1 };
+int grid_plan_status(grid_plan_t plan, unsigned* flags, int reset);
 
 /*
  * Compression (Sec. 2.2, last paragraph, after Muscat): adjacent visibilities

@@ -55,13 +55,15 @@ class Plan:
     """Owns one grid_plan_t (destroyed on close() or garbage collection).
 
     schedule: "chunked" (fixed visibilities per team, global flushes), "patch" (chunks binned by
-    grid patch, flushes into a shared-memory window), or "tile" (grids as "chunked"; degrids by
-    tile gather, one warp per 32 visibilities, threads a multiple of 32).
+    grid patch, flushes into a shared-memory window), "tile" (grids as "chunked"; degrids by
+    tile gather, one warp per 32 visibilities, threads a multiple of 32), or "lazy" (grids with a
+    bin of bin_u x bin_v cells, wider than the paper's, whose box moves only when the footprint
+    leaves it; degrids as "chunked").
     """
 
     def __init__(self, G: int, S: int, oversample: int, npol: int, B: int = 1, Bu: int | None = None,
                  Bv: int | None = None, vis_per_chunk: int = 0, threads: int = 0, precision: str = "f32",
-                 schedule: str = "chunked", patch: int = 0):
+                 schedule: str = "chunked", patch: int = 0, bin_u: int = 0, bin_v: int = 0):
         lib = _lib.load()
         d = _lib.GridPlanDesc()
         lib.grid_plan_desc_init(ctypes.byref(d), G, S, oversample, npol, B)
@@ -72,6 +74,8 @@ class Plan:
         d.precision = PREC[precision]
         d.schedule = SCHED[schedule]
         d.patch = patch
+        d.bin_u = bin_u
+        d.bin_v = bin_v
         h = ctypes.c_void_p()
         _lib.check(lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)))
         self._h = h
@@ -97,6 +101,12 @@ class Plan:
     def skipped(self, reset: bool = False) -> int:
         v = ctypes.c_int64()
         _lib.check(_lib.load().grid_plan_skipped(self.handle, ctypes.byref(v), int(reset)))
+        return v.value
+
+    def status(self, reset: bool = False) -> int:
+        """Status flags of the plan's gridding calls (bit 0: a bulk copy of records timed out)."""
+        v = ctypes.c_uint()
+        _lib.check(_lib.load().grid_plan_status(self.handle, ctypes.byref(v), int(reset)))
         return v.value
 
     def close(self) -> None:

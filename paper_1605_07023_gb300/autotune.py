@@ -66,7 +66,8 @@ def save_cache(c: dict) -> None:
 
 def plan_kwargs(cfg: dict) -> dict:
     return dict(Bu=cfg["Bu"], Bv=cfg["Bv"], schedule=cfg["schedule"], vis_per_chunk=cfg.get("vis_per_chunk", 0),
-                threads=cfg.get("threads", 0), precision=cfg.get("precision", "f32"))
+                threads=cfg.get("threads", 0), precision=cfg.get("precision", "f32"), bin_u=cfg.get("bin_u", 0),
+                bin_v=cfg.get("bin_v", 0))
 
 
 def _candidates(kind: str):

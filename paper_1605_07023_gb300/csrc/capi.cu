@@ -28,6 +28,12 @@ struct grid_plan_s {
   int tile_threads;
   size_t tile_smem;
   int occ_tile;            // resident tile-degridding CTAs per SM
+  const LazyEntry* lazy;   // lazy-box schedule: the gridding kernel, its geometry and launch shape
+  Geometry gl;             // the widened bin (nu, nv, ts) of the lazy gridder
+  int lazy_threads;
+  int lazy_teams;          // teams per CTA
+  int seg;                 // lanes per team slot
+  size_t lazy_smem;
   unsigned long long* d_skipped;
   PatchScratch ps;
   long long ps_chunks_cap;  // chunk capacity of the patch scratch
@@ -60,6 +66,14 @@ int cuda_fail(cudaError_t e, const char* what) {
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 int ilog2(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
 size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+const LazyEntry* find_lazy_kernel(int bu, int bv, int p) {
+  int n = 0;
+  const LazyEntry* t = p == 1 ? lazy_kernels_p1(&n) : p == 2 ? lazy_kernels_p2(&n) : p == 4 ? lazy_kernels_p4(&n) : nullptr;
+  for (int i = 0; t && i < n; ++i)
+    if (t[i].bu == bu && t[i].bv == bv) return &t[i];
+  return nullptr;
+}
 
 const KernelEntry* find_kernel(int bu, int bv, int p) {
   int n = 0;
@@ -167,6 +181,7 @@ void grid_plan_desc_init(grid_plan_desc* d, int G, int S, int oversample, int np
   memset(d, 0, sizeof *d);
   d->G = G; d->S = S; d->oversample = oversample; d->npol = npol; d->Bu = B; d->Bv = B;
   d->vis_per_chunk = 0; d->threads = 0; d->precision = GRID_PREC_F32; d->schedule = GRID_SCHED_CHUNKED; d->patch = 0;
+  d->bin_u = 0; d->bin_v = 0;
 }
 
 int grid_plan_create(grid_plan_t* out, int G, int S, int oversample, int npol, int B) {
@@ -186,13 +201,22 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   if (d.npol != 1 && d.npol != 2 && d.npol != 4) return fail(GRID_ERR_INVALID, "npol=%d: must be 1, 2 or 4", d.npol);
   if (d.Bu < 1 || d.Bu > 8 || d.Bv < 1 || d.Bv > 8) return fail(GRID_ERR_INVALID, "B=(%d,%d): must be 1..8", d.Bu, d.Bv);
   if (d.precision < GRID_PREC_F32 || d.precision > GRID_PREC_F16) return fail(GRID_ERR_INVALID, "precision=%d", d.precision);
-  if (d.schedule != GRID_SCHED_CHUNKED && d.schedule != GRID_SCHED_PATCH && d.schedule != GRID_SCHED_TILE)
+  if (d.schedule != GRID_SCHED_CHUNKED && d.schedule != GRID_SCHED_PATCH && d.schedule != GRID_SCHED_TILE &&
+      d.schedule != GRID_SCHED_LAZY)
     return fail(GRID_ERR_INVALID, "schedule=%d", d.schedule);
-  if (d.threads % 32 != 0 && d.schedule == GRID_SCHED_TILE)
-    return fail(GRID_ERR_INVALID, "threads=%d: the tile schedule needs whole warps", d.threads);
+  if (d.threads % 32 != 0 && (d.schedule == GRID_SCHED_TILE || d.schedule == GRID_SCHED_LAZY))
+    return fail(GRID_ERR_INVALID, "threads=%d: the tile and lazy schedules need whole warps", d.threads);
+  if (d.schedule != GRID_SCHED_LAZY && (d.bin_u != 0 || d.bin_v != 0))
+    return fail(GRID_ERR_INVALID, "bin_u/bin_v apply to the lazy schedule only");
   if (d.vis_per_chunk < 0 || d.vis_per_chunk > (1 << 20)) return fail(GRID_ERR_INVALID, "vis_per_chunk=%d", d.vis_per_chunk);
   if (d.threads < 0 || d.threads > 1024) return fail(GRID_ERR_INVALID, "threads=%d", d.threads);
-  const KernelEntry* k = find_kernel(d.Bu, d.Bv, d.npol);
+  // the chunked kernels of the plan's shape; a lazy-schedule shape that has none degrids with 2x2 blocks
+  int kbu = d.Bu, kbv = d.Bv;
+  const KernelEntry* k = find_kernel(kbu, kbv, d.npol);
+  if (!k && d.schedule == GRID_SCHED_LAZY) {
+    kbu = kbv = 2;
+    k = find_kernel(kbu, kbv, d.npol);
+  }
   if (!k) return fail(GRID_ERR_UNSUPPORTED, "no kernel built for Bu=%d Bv=%d npol=%d", d.Bu, d.Bv, d.npol);
 
   grid_plan_s* pl = new grid_plan_s;
@@ -200,7 +224,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   pl->k = k;
   Geometry& g = pl->g;
   g.G = d.G; g.S = d.S; g.O = d.oversample; g.log2O = ilog2(d.oversample); g.h = (d.S - 1) / 2; g.P = d.npol;
-  finish_geometry(g, d.Bu, d.Bv);
+  finish_geometry(g, kbu, kbv);
 
   cudaError_t e = cudaGetDevice(&pl->device);
   if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaGetDevice"); }
@@ -229,7 +253,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   if (d.vis_per_chunk == 0) d.vis_per_chunk = d.schedule == GRID_SCHED_PATCH ? 64 : 256;
   pl->chunk_len = d.vis_per_chunk;
 
-  const size_t tb = tables_bytes(g, d.Bu, d.Bv);
+  const size_t tb = tables_bytes(g, kbu, kbv);
   if (tb > 96 * 1024) {
     delete pl;
     return fail(GRID_ERR_UNSUPPORTED, "padded GCF tables need %zu bytes of shared memory (> 96 KiB)", tb);
@@ -309,9 +333,58 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor (tile)"); }
     if (pl->occ_tile < 1) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "tile degridding kernel cannot be resident"); }
   }
-  e = cudaMalloc(&pl->d_skipped, sizeof(unsigned long long));
+  if (d.schedule == GRID_SCHED_LAZY) {
+    const LazyEntry* lk = find_lazy_kernel(d.Bu, d.Bv, d.npol);
+    if (!lk) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "lazy schedule: no kernel for Bu=%d Bv=%d npol=%d", d.Bu, d.Bv, d.npol); }
+    // default bin: the paper's, widened by one block along each axis where it leaves a footprint
+    // less than a block of room, while the team stays within a warp
+    // the paper's bin for these blocks (Sec. 3): the smallest multiple of B that holds S + B - 1 cells
+    const int mbu = ((d.S + 2 * d.Bu - 2) / d.Bu) * d.Bu, mbv = ((d.S + 2 * d.Bv - 2) / d.Bv) * d.Bv;
+    if (d.bin_u == 0) d.bin_u = mbu + (mbu - d.S < d.Bu && (mbu / d.Bu + 1) * (mbv / d.Bv) <= 32 ? d.Bu : 0);
+    if (d.bin_v == 0) d.bin_v = mbv + (mbv - d.S < d.Bv && (d.bin_u / d.Bu) * (mbv / d.Bv + 1) <= 32 ? d.Bv : 0);
+    if (d.bin_u % d.Bu || d.bin_v % d.Bv || d.bin_u < mbu || d.bin_v < mbv || d.bin_u > 1024 || d.bin_v > 1024) {
+      const int bu = d.bin_u, bv = d.bin_v, mu = mbu, mv = mbv;
+      delete pl;
+      return fail(GRID_ERR_INVALID, "bin %dx%d: sides must be multiples of (Bu, Bv) and at least %dx%d", bu, bv, mu, mv);
+    }
+    Geometry& gl = pl->gl;
+    gl = g;
+    gl.nu = d.bin_u / d.Bu;
+    gl.nv = d.bin_v / d.Bv;
+    gl.nbu = d.bin_u;
+    gl.nbv = d.bin_v;
+    gl.ts = gl.nu * gl.nv;
+    gl.nuB = gl.nbu;
+    gl.nvB = gl.nbv;
+    gl.mu = (unsigned)((1ull << 31) / (unsigned)gl.nu + 1);
+    gl.mv = (unsigned)((1ull << 31) / (unsigned)gl.nv + 1);
+    if (gl.ts > 32) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "lazy schedule: %d threads per team (more than a warp)", gl.ts); }
+    int seg = 1;
+    while (seg < gl.ts) seg <<= 1;
+    cudaFuncAttributes fa_l;
+    e = cudaFuncGetAttributes(&fa_l, lk->fn);
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncGetAttributes (lazy)"); }
+    int warps = (d.threads > 0 ? d.threads : 128) / 32;
+    if (warps * 32 > fa_l.maxThreadsPerBlock) warps = fa_l.maxThreadsPerBlock / 32;
+    while (warps > 1 && lk->smem(gl, warps * (32 / seg)) + fa_l.sharedSizeBytes > smem_max) --warps;
+    const size_t sm = lk->smem(gl, warps * (32 / seg));
+    if (warps < 1 || sm + fa_l.sharedSizeBytes > smem_max) {
+      delete pl;
+      return fail(GRID_ERR_UNSUPPORTED, "lazy schedule: tables and records do not fit in shared memory");
+    }
+    e = cudaFuncSetAttribute(lk->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_l.sharedSizeBytes));
+    if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute (lazy)"); }
+    gl.tpc = warps * (32 / seg);
+    pl->lazy = lk;
+    pl->seg = seg;
+    pl->lazy_threads = warps * 32;
+    pl->lazy_teams = gl.tpc;
+    pl->lazy_smem = sm;
+  }
+  // word 0: skipped visibilities; word 1: status flags of the lazy gridder
+  e = cudaMalloc(&pl->d_skipped, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) { delete pl; return fail(GRID_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
-  e = cudaMemset(pl->d_skipped, 0, sizeof(unsigned long long));
+  e = cudaMemset(pl->d_skipped, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) { cudaFree(pl->d_skipped); delete pl; return cuda_fail(e, "cudaMemset"); }
   pl->desc = d;
   *out = pl;
@@ -332,10 +405,11 @@ void grid_plan_destroy(grid_plan_t pl) {
 
 int grid_plan_describe(grid_plan_t pl, grid_plan_desc* desc, int* bin_u, int* bin_v, int* team_size) {
   if (!pl) return fail(GRID_ERR_INVALID, "null plan");
-  if (desc) { *desc = pl->desc; desc->threads = pl->threads; }
-  if (bin_u) *bin_u = pl->g.nbu;
-  if (bin_v) *bin_v = pl->g.nbv;
-  if (team_size) *team_size = pl->g.ts;
+  const Geometry& g = pl->lazy ? pl->gl : pl->g;
+  if (desc) { *desc = pl->desc; desc->threads = pl->lazy ? pl->lazy_threads : pl->threads; }
+  if (bin_u) *bin_u = g.nbu;
+  if (bin_v) *bin_v = g.nbv;
+  if (team_size) *team_size = g.ts;
   return GRID_OK;
 }
 
@@ -363,6 +437,17 @@ int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const
   a.table = kernel_table;
   a.grid = (float2*)grid_out;
   cudaError_t e;
+  if (pl->lazy) {
+    a.g = pl->gl;
+    a.seg = pl->seg;
+    a.status = (unsigned*)(pl->d_skipped + 1);
+    const long long blocks = (a.n_chunks + pl->lazy_teams - 1) / pl->lazy_teams;
+    if (blocks > 0x7FFFFFFFLL) return fail(GRID_ERR_INVALID, "too many chunks");
+    void* args[] = {&a};
+    e = cudaLaunchKernel(pl->lazy->fn, dim3((unsigned)blocks), dim3(pl->lazy_threads), args, pl->lazy_smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid (lazy) kernel launch");
+    return GRID_OK;
+  }
   if (pl->desc.schedule != GRID_SCHED_PATCH) {
     const long long blocks = (a.n_chunks + pl->g.tpc - 1) / pl->g.tpc;
     void* args[] = {&a};
@@ -466,6 +551,22 @@ int grid_plan_skipped(grid_plan_t pl, int64_t* n_skipped, int reset) {
   if (reset) {
     e = cudaMemset(pl->d_skipped, 0, sizeof v);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  }
+  return GRID_OK;
+}
+
+int grid_plan_status(grid_plan_t pl, unsigned* flags, int reset) {
+  g_err.clear();
+  if (!pl || !flags) return fail(GRID_ERR_INVALID, "null argument");
+  int rc = check_device(pl);
+  if (rc) return rc;
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpy(&v, pl->d_skipped + 1, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (status)");
+  *flags = (unsigned)v;
+  if (reset) {
+    e = cudaMemset(pl->d_skipped + 1, 0, sizeof v);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset (status)");
   }
   return GRID_OK;
 }

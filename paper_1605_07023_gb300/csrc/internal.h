@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "kernels.cuh"
+#include "lazy.cuh"
 
 namespace gbg {
 
@@ -30,6 +31,11 @@ struct PatchScratch {
 const KernelEntry* kernels_p1(int* n);
 const KernelEntry* kernels_p2(int* n);
 const KernelEntry* kernels_p4(int* n);
+
+// Lazy-box gridders (inst_lazy_p*.cu), one per (Bu, Bv, P) that is built.
+const LazyEntry* lazy_kernels_p1(int* n);
+const LazyEntry* lazy_kernels_p2(int* n);
+const LazyEntry* lazy_kernels_p4(int* n);
 
 // Tile-gather degridding (degrid_tile.cu), one kernel per (S, P).
 struct TileKernel {

@@ -66,9 +66,9 @@ __host__ __device__ inline void finish_geometry(Geometry& g, int BU, int BV) {
   g.mv = (unsigned)((1ull << 31) / (unsigned)g.nv + 1);
 }
 
-// q mod n for 0 <= q < 2^15, with m = floor(2^31/n) + 1: floor(q*m / 2^31) =
-// floor(q/n + q*e/2^31) with 0 < e <= 1, and q*e/2^31 < 2^-16 < 1/n, so the
-// quotient is exact.
+// q mod n for 0 <= q < 2^31/n (so for q < 2^15 with any n <= 2^16), with
+// m = floor(2^31/n) + 1: floor(q*m / 2^31) = floor(q/n + q*e/2^31) with
+// 0 < e <= 1, and q*e/2^31 < 1/n, so the quotient is exact.
 __device__ __forceinline__ int mod_small(int q, int n, unsigned m) {
   return q - n * (int)__umulhi((unsigned)q << 1, m);
 }
@@ -92,6 +92,8 @@ struct Args {
   int* work_next;         // device work counter (persistent CTAs)
   int win;                // patch window side in cells (patch + halo); 0 = chunked schedule
   int warp_sync;          // 1: every team lies inside one warp (team size divides 32), teams sync per warp
+  int seg;                // lazy-box gridder: lanes per team slot (a power of two >= team size, <= 32)
+  unsigned* status;       // lazy-box gridder: bit 0 set when a bulk copy did not complete in time
   unsigned long long* skipped;
 };
 

@@ -38,7 +38,9 @@ def test_degrid_candidates_include_the_tile_schedule_in_whole_warps():
 def test_plan_kwargs_pass_every_field():
     cfg = dict(schedule="tile", Bu=2, Bv=2, vis_per_chunk=0, threads=64)
     kw = autotune.plan_kwargs(cfg)
-    assert kw == dict(Bu=2, Bv=2, schedule="tile", vis_per_chunk=0, threads=64, precision="f32")
+    assert kw == dict(Bu=2, Bv=2, schedule="tile", vis_per_chunk=0, threads=64, precision="f32", bin_u=0, bin_v=0)
+    kw = autotune.plan_kwargs(dict(schedule="lazy", Bu=4, Bv=2, vis_per_chunk=512, threads=128, bin_u=12, bin_v=10))
+    assert (kw["schedule"], kw["bin_u"], kw["bin_v"]) == ("lazy", 12, 10)
 
 
 def test_cache_key_depends_on_problem_and_candidates(monkeypatch):

@@ -91,14 +91,16 @@ def test_newer_entry_points_reject_bad_arguments(lib):
 
 
 def test_schedule_and_tile_threads_checked_on_the_host(lib):
-    """Unknown schedules, and a tile-schedule CTA size that is not whole warps, are rejected before
-    any device call."""
+    """Unknown schedules, tile- and lazy-schedule CTA sizes that are not whole warps, and bin widths
+    given to a schedule other than the lazy one are rejected before any device call."""
     from paper_1605_07023_gb300 import _lib
     h = ctypes.c_void_p()
-    for sched, threads in [(3, 0), (-1, 0), (_lib.SCHED["tile"], 48), (_lib.SCHED["tile"], 100)]:
+    for sched, threads, bins in [(4, 0, 0), (-1, 0, 0), (_lib.SCHED["tile"], 48, 0), (_lib.SCHED["tile"], 100, 0),
+                                 (_lib.SCHED["lazy"], 48, 0), (_lib.SCHED["chunked"], 0, 10)]:
         d = _lib.GridPlanDesc()
         lib.grid_plan_desc_init(ctypes.byref(d), 256, 7, 8, 4, 2)
         d.schedule = sched
         d.threads = threads
-        assert lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == _lib.GRID_ERR_INVALID, (sched, threads)
+        d.bin_u = bins
+        assert lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == _lib.GRID_ERR_INVALID, (sched, threads, bins)
         assert not h.value
