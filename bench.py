@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--vis", type=int, default=0, help="use only the first N visibilities (profiling runs)")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain Romein kernel (profiling runs)")
     ap.add_argument("--no-compression", action="store_true", help="skip the compression measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the coarsening sweep and the single-pol comparison")
     return ap.parse_args()
 
 
@@ -171,6 +172,59 @@ def cpu_oracle_rate(w, n_sample: int, table64):
     return 2 * n_valid * w.S * w.S / dt, dt
 
 
+def oracle_threads(w, table64, n_threads: int):
+    """The same oracle on n_threads host cores: grid, then degrid of the gridded result.
+
+    The oracle's C routines run unchanged, several at once from Python threads (the binding releases
+    the GIL). Gridding: visibilities whose footprint rows lie wholly inside one of n_threads bands of
+    grid rows are gridded by that band's thread straight into one shared grid (the bands are
+    disjoint, so no two threads add to the same cell); the few that straddle a band edge are gridded
+    afterwards by one thread. Degridding: disjoint slices of the visibilities, one per thread. The
+    sums equal the single-thread oracle's up to the order of additions.
+    Returns (grid, degridded values, skipped count, seconds).
+    """
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    cell, _, _ = oracle.indices(w.G, w.S, w.oversample, w.uv)
+    h = (w.S - 1) // 2
+    valid = cell[:, 1] >= 0
+    lo = cell[:, 1] - h
+    band = max(1, -(-w.G // n_threads))
+    b0 = np.where(valid, lo // band, -1)
+    inside = valid & ((lo + w.S - 1) // band == b0)
+    g = np.zeros((w.npol, w.G, w.G), np.complex128)
+    parts = [np.flatnonzero(inside & (b0 == b)) for b in range(n_threads)]
+    rest = np.flatnonzero(~inside)
+
+    def grid_part(idx):
+        if idx.size:
+            oracle.grid(w.G, w.S, w.oversample, w.uv[idx], w.vis[idx], w.weights[idx], table64, out=g)
+
+    with cf.ThreadPoolExecutor(n_threads) as ex:
+        list(ex.map(grid_part, parts))
+    skipped = 0
+    if rest.size:
+        _, skipped = oracle.grid(w.G, w.S, w.oversample, w.uv[rest], w.vis[rest], w.weights[rest], table64, out=g)
+    slices = np.array_split(np.arange(w.n_vis), n_threads)
+    out = np.empty((w.n_vis, w.npol), np.complex128)
+
+    def degrid_part(idx):
+        if idx.size:
+            out[idx] = oracle.degrid(w.G, w.S, w.oversample, w.uv[idx], g, table64)[0]
+
+    with cf.ThreadPoolExecutor(n_threads) as ex:
+        list(ex.map(degrid_part, slices))
+    return g, out, skipped, time.perf_counter() - t0
+
+
+def cpu_oracle_rate_threads(w, table64, n_threads: int):
+    """vis-taps/s of grid + degrid of the whole batch by the oracle on n_threads host cores."""
+    _, _, skipped, dt = oracle_threads(w, table64, n_threads)
+    return 2 * (w.n_vis - skipped) * w.S * w.S / dt, dt
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -179,12 +233,12 @@ def run_reference(args):
     import oracle
     oracle.build()
     table64 = oracle.kb_table(w.S, w.oversample, w.beta).astype(np.float32).astype(np.float64)
-    n_sample = w.n_vis
+    n_cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_oracle_rate(w, 20_000, table64)
+        cpu_oracle_rate_threads(synth.scaled_down(w, 20_000), table64, n_cores)
     rates, times = [], []
     for _ in range(args.steps):
-        r, dt = cpu_oracle_rate(w, n_sample, table64)
+        r, dt = cpu_oracle_rate_threads(w, table64, n_cores)
         rates.append(r)
         times.append(dt)
     value = float(np.mean(rates))
@@ -193,8 +247,9 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": "the whole batch per step (warm-up steps use 20,000 visibilities)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"all {n_sample} visibilities per step, grid + degrid, FP64, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_cores, "kind": "oracle",
+                         "sample": f"all {w.n_vis} visibilities per step, grid + degrid, FP64, the unchanged oracle on "
+                                   f"{n_cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -266,6 +321,95 @@ def measure_compression(gb, autotune, torch, dev, cfg_grid, cfg_degrid, steps, w
             "ms_per_step_uncompressed": t0, "ms_per_step_compressed": t1, "compress_ms": tc, "expand_ms": te,
             "value_uncompressed": taps / (t0 / 1e3), "value_compressed": taps / (t1 / 1e3),
             "unit": "original vis-taps/s (grid + degrid)"}
+
+
+SWEEP_SHAPES = [(1, 1), (2, 1), (1, 2), (2, 2), (4, 1), (1, 4), (4, 2), (2, 4), (3, 3), (4, 4), (8, 1), (1, 8), (8, 2), (2, 8)]
+SWEEP_WORK = [(128, 128), (256, 128), (1024, 256)]   # (visibilities per team chunk, threads per CTA)
+
+
+def time_grid(gb, plan, uv, vis, wt, table, g, reps=3):
+    """Median CUDA-event time (ms) of grid() after two warm-up calls; the grid is zeroed outside the timing."""
+    import torch
+    for _ in range(2):
+        gb.grid(plan, uv, vis, wt, table, g)
+    ms = []
+    for _ in range(reps):
+        g.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gb.grid(plan, uv, vis, wt, table, g)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def measure_sweep(gb, w, uv, vis, wt, table, g, n_valid, peak):
+    """Sec. 5's central comparison on this workload: gridding time and FP32 FMA fraction for every
+    built coarsening shape with Bu*Bv <= 16 (the paper's sweep), each at its fastest chunk length and
+    CTA size among SWEEP_WORK (chunked schedule, global flushes)."""
+    rows = []
+    gpa = n_valid * w.S * w.S * w.npol
+    for bu, bv in SWEEP_SHAPES:
+        best = None
+        for L, T in SWEEP_WORK:
+            try:
+                plan = gb.Plan(w.G, w.S, w.oversample, w.npol, Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
+            except gb.GridderError:
+                continue
+            ms = time_grid(gb, plan, uv, vis, wt, table, g)
+            plan.close()
+            if best is None or ms < best[0]:
+                best = (ms, L, T)
+        if best is None:
+            continue
+        ms, L, T = best
+        rows.append({"Bu": bu, "Bv": bv, "grid_ms": ms, "vis_per_chunk": L, "threads": T,
+                     "grid_fma_frac": fma_fraction(gpa / (ms / 1e3), peak)})
+    g.zero_()
+    plain = next((r for r in rows if (r["Bu"], r["Bv"]) == (1, 1)), None)
+    best = min(rows, key=lambda r: r["grid_ms"]) if rows else None
+    return {"workload": "quad-pol (the bench workload), gridding only", "shapes": rows,
+            "best": {k: best[k] for k in ("Bu", "Bv", "grid_ms", "grid_fma_frac")} if best else None,
+            "gain_vs_1x1": (plain["grid_ms"] / best["grid_ms"]) if plain and best else None,
+            "paper_context": "Sec. 5: coarsening gains of 1.9x (quad-pol) and 3.2x (single-pol) on a GTX 980"}
+
+
+SINGLE_POL_CANDIDATES = [(2, 2, 256, 128), (4, 2, 256, 128), (2, 4, 256, 128), (4, 4, 256, 128), (3, 3, 256, 128),
+                         (8, 2, 256, 128), (4, 2, 1024, 256), (4, 2, 128, 128)]
+
+
+def measure_single_pol(gb, torch, dev, peak):
+    """The single-polarization coarsening gain at throughput scale (Sec. 5 reports 3.2x on a GTX 980):
+    the precision workload (G=4096, S=15, O=16, P=1, 16,711,680 visibilities, FP32) gridded by the plain
+    Romein kernel (B=1, 1024 visibilities per team) and by the fastest coarsened configuration among
+    SINGLE_POL_CANDIDATES, in the same run."""
+    w = synth.precision_single_pol()
+    uv = torch.from_numpy(w.uv).to(dev)
+    vis = torch.from_numpy(w.vis).to(dev)
+    wt = torch.from_numpy(w.weights).to(dev)
+    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta, device=dev)
+    g = torch.zeros((1, w.G, w.G), dtype=torch.complex64, device=dev)
+    gpa = w.n_vis * w.S * w.S
+    plain = gb.Plan(w.G, w.S, w.oversample, 1, B=1, vis_per_chunk=1024, schedule="chunked")
+    p_ms = time_grid(gb, plain, uv, vis, wt, table, g)
+    plain.close()
+    best = None
+    for bu, bv, L, T in SINGLE_POL_CANDIDATES:
+        plan = gb.Plan(w.G, w.S, w.oversample, 1, Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
+        ms = time_grid(gb, plan, uv, vis, wt, table, g)
+        plan.close()
+        if best is None or ms < best[0]:
+            best = (ms, bu, bv, L, T)
+    ms, bu, bv, L, T = best
+    del uv, vis, wt, g
+    torch.cuda.empty_cache()
+    return {"workload": "precision single-pol: G=4096 S=15 O=16 P=1, 256 antennas, 32,640 bl x 256 t x 2 ch = "
+                        "16,711,680 vis, FP32", "plain_grid_ms": p_ms,
+            "coarsened": {"Bu": bu, "Bv": bv, "vis_per_chunk": L, "threads": T, "grid_ms": ms},
+            "gain": p_ms / ms, "plain_fma_frac": fma_fraction(gpa / (p_ms / 1e3), peak),
+            "coarsened_fma_frac": fma_fraction(gpa / (ms / 1e3), peak),
+            "paper_context": "Sec. 5: 3.2x single-pol coarsening gain on a GTX 980"}
 
 
 def parse_cfg(s):
@@ -371,10 +515,13 @@ def main():
         p_total, p_g, p_d = timed(pplan, pplan, args.steps, args.warmup)
     p_value = 2.0 * n_valid * S2 / (p_total / args.steps / 1e3)
 
+    sweep = single = None
     info = gb.device_info()
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or info["max_clock_khz"] / 1e3
-    peak = fma_peak_tflops(info["sm_count"], max_mhz)
+    derived_peak = fma_peak_tflops(info["sm_count"], max_mhz)
+    # the denominator: FP32 FMA throughput measured in this run by the library's own FFMA2 kernel
+    peak = max(gb.measure_fma_peak(iters=32768) for _ in range(3))
     useful_flops = FLOPS_PER_GPA * n_valid * S2 * w.npol  # 2 FFMA (4 flop) per useful grid-point addition
     gpa_g = n_valid * S2 * w.npol / (g_ms / 1e3)
     gpa_d = n_valid * S2 * w.npol / (d_ms / 1e3)
@@ -383,6 +530,10 @@ def main():
     pg_tflops = useful_flops / (p_g / 1e3) / 1e12
     dominant = "grid" if g_ms >= d_ms else ("degrid_tile" if best_degrid["schedule"] == "tile" else "degrid")
     achieved = g_tflops if dominant == "grid" else d_tflops
+
+    if not args.no_sweep and not args.vis:
+        sweep = measure_sweep(gb, w, uv, vis, wt, table, grid_buf, n_valid, peak)
+        single = measure_single_pol(gb, torch, dev, peak)
 
     # DRAM bytes per launch from one ncu capture (profiles/traffic.json), used only while the
     # kernel's source file is the one that was captured
@@ -441,8 +592,19 @@ def main():
             r, dt = cpu_oracle_rate(w, w.n_vis, table64)
             rates.append(r)
             spent += dt
-        cpu = {"value": float(np.mean(rates)), "unit": UNIT, "cores": 1, "kind": "oracle",
+        one = {"value": float(np.mean(rates)), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"all {w.n_vis} visibilities x {len(rates)}, grid + degrid, FP64, 1 thread ({spent:.1f} s)"}
+        n_cores = os.cpu_count() or 1
+        prates, pspent = [], 0.0
+        while pspent < 4.0 and len(prates) < 4:
+            r, dt = cpu_oracle_rate_threads(w, table64, n_cores)
+            prates.append(r)
+            pspent += dt
+        cpu = {"value": float(np.mean(prates)), "unit": UNIT, "cores": n_cores, "kind": "oracle",
+               "sample": f"all {w.n_vis} visibilities x {len(prates)}, grid + degrid, FP64, the unchanged oracle "
+                         f"on {n_cores} threads (gridding by disjoint bands of grid rows, degridding by disjoint "
+                         f"slices) ({pspent:.1f} s)",
+               "single_core": one}
 
     comp = None
     if not args.no_compression and not args.vis:
@@ -468,8 +630,10 @@ def main():
             "speedup_vs_plain": value / p_value, "grid_speedup_vs_plain": p_g / g_ms,
             "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_note": f"{info['sm_count']} SMs x 128 FP32 FMA lanes x 2 flop x {max_mhz:.0f} MHz; "
-                                      "achieved counts 4 flop per useful grid-point addition (real taps), padding excluded"},
+                         "peak_note": "measured in this run: grid_measure_fma_peak (independent FFMA2 chains, 64 warps "
+                                      f"per SM); derived {info['sm_count']} SMs x 128 FP32 FMA lanes x 2 flop x "
+                                      f"{max_mhz:.0f} MHz = {derived_peak:.1f}; achieved counts 4 flop per useful "
+                                      "grid-point addition (real taps), padding excluded"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "n_valid_vis": n_valid,
@@ -480,6 +644,10 @@ def main():
             line["cpu_baseline"] = cpu
         if comp is not None:
             line["compression"] = comp
+        if sweep is not None:
+            line["sweep"] = sweep
+        if single is not None:
+            line["single_pol"] = single
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -183,18 +183,25 @@ int degrid_weighted(grid_plan_t plan, int64_t n_vis, const double* uv, const voi
 int grid_make_kernel_table(int S, int oversample, double beta, int precision, void* table_out, cudaStream_t stream);
 
 /*
- * The per-visibility indices the kernels use, for bit-exact checking:
+ * The per-visibility indices the kernels use, for bit-exact checking (a test
+ * hook). The passage they follow is Sec. 2.2's: a visibility is snapped to
+ * the nearest point of the oversampled grid, which fixes its cell and the GCF
+ * row; the exact rounding rule is the one in the conventions above.
  *   cell[n][2] = (C_u, C_v) and sub[n][2] = (r_u, r_v), or (-1, -1) for both
  *   when the visibility is skipped.
- * Device pointers, int32.
+ * Device pointers, int32, caller-owned, n_vis entries each; the call is
+ * asynchronous on `stream`. GRID_ERR_INVALID for a null or misaligned
+ * pointer.
  */
 int grid_compute_indices(grid_plan_t plan, int64_t n_vis, const double* uv, int32_t* cell, int32_t* sub,
                          cudaStream_t stream);
 
 /*
  * Number of visibilities skipped (invalid or off the grid) by the plan's calls
- * since it was created or last reset. This synchronises with the plan's
- * device counter. reset != 0 zeroes the counter afterwards.
+ * since it was created or last reset. A bookkeeping call with no passage of
+ * its own: it reports the edge rule of the conventions above (the paper is
+ * silent on footprints that leave the grid). This synchronises with the
+ * plan's device counter. reset != 0 zeroes the counter afterwards.
  */
 int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
 
@@ -359,17 +366,20 @@ const char* grid_batch_last_error(void);
  * Gridding without device allocation. The paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc:
  *  - a real-time pipeline that reserves all of its device memory at start-up
- *    and may not allocate while observing;
- *  - code that runs while a stream is being captured into a CUDA graph;
- *  - a host framework that owns the device heap through its own allocator.
+ *    and may not allocate while observing (an allocation can stall or fail
+ *    part way through);
+ *  - a host framework that owns the device heap through its own allocator,
+ *    whose accounting a library allocating behind its back would break.
  * Such callers cannot create a plan, because grid_plan_create and the patch
  * schedule allocate scratch.
  *
  * grid_patch_static() takes the plan parameters directly and grids exactly
  * as grid() does with GRID_SCHED_PATCH and 64-visibility chunks. The other
- * arguments and the accumulate semantics are those of grid(). Its binning
- * scratch lives in one file-scope device array of about 1.9 MB, which every
- * GPU that loads the library holds until the process exits.
+ * arguments and the accumulate semantics are those of grid(), except that
+ * skipped (invalid or off-grid) visibilities are not reported: there is no
+ * plan to read a count from. Its binning scratch lives in one file-scope
+ * device array of about 1.9 MB, which every GPU that loads the library holds
+ * until the process exits.
  *  - Limits: at most 8,388,608 visibilities per call and at most 16,384 grid
  *    patches (patches are 32 cells at npol 4, 48 at npol 2, 96 at npol 1).
  *    A larger call returns GRID_ERR_INVALID with a message and queues
@@ -377,8 +387,10 @@ const char* grid_batch_last_error(void);
  *  - Allocation: it calls no cudaMalloc, no cudaFree and no allocating
  *    library routine; it only enqueues memsets and kernels on `stream`.
  *  - First call: the first call on each device looks up the array's device
- *    address (cudaGetSymbolAddress) with that device current. Make that first
- *    call before any stream capture.
+ *    address (cudaGetSymbolAddress) with that device current and keeps it for
+ *    the life of the process. Make that first call before any stream capture.
+ *    Do not use the entry point across cudaDeviceReset (the kept address
+ *    would be stale).
  *  - Concurrency: all calls share the one array. Calls whose work overlaps
  *    on the GPU (other streams, other host threads) race and give wrong
  *    results; serialise them.
@@ -411,6 +423,18 @@ int grid_tap_form(int Bu, int Bv, int npol, int* form, int* multiplies);
 
 /* Peak FP32 FMA lanes per SM per clock (128 on sm_103) and the SM count of the current device. */
 int grid_device_info(int* sm_count, int* fma_lanes_per_sm, int* max_clock_khz);
+
+/*
+ * Measured FP32 FMA throughput of the current device, the denominator of the
+ * "% of FP32 FMA peak" figures (Sec. 5 quotes efficiency against the GPU's
+ * FP32 peak; here the peak is measured rather than derived). Runs a kernel of
+ * independent packed FMA chains (iters iterations of 8 FFMA2 per thread, 64
+ * warps per SM) once to warm up and once timed with CUDA events on `stream`,
+ * then synchronises. *tflops = 4 flop x FFMA2 lanes x instructions / time
+ * (2 FMAs per FFMA2, 2 flop per FMA). iters 1 .. 2^24; a few thousand make a
+ * launch of some milliseconds. Host call; allocates nothing on the device.
+ */
+int grid_measure_fma_peak(int iters, double* tflops, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

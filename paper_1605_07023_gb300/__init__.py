@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import GridderError, PREC, SCHED
 
 __all__ = ["Plan", "BatchPlan", "grid_plan_create", "grid_plan_create_ex", "grid", "degrid", "degrid_weighted", "grid_make_kernel_table",
-           "grid_compute_indices", "device_info", "tap_form", "GridderError"]
+           "grid_compute_indices", "device_info", "tap_form", "measure_fma_peak", "GridderError"]
 
 
 def _torch():
@@ -340,6 +340,13 @@ def device_info() -> dict:
 
 
 TAP_FORMS = ("product", "factor_v", "factor_u")
+
+
+def measure_fma_peak(iters: int = 4096, stream=None) -> float:
+    """grid_measure_fma_peak(): the device's measured FP32 FMA rate in TFLOP/s (synchronises)."""
+    v = ctypes.c_double()
+    _lib.check(_lib.load().grid_measure_fma_peak(int(iters), ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 def tap_form(Bu: int, Bv: int, npol: int) -> tuple[str, int]:

@@ -25,7 +25,7 @@ EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "gr
            "grid_last_error", "grid_device_info", "grid_tap_form", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
            "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
            "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host", "grid_batch_create_ex",
-           "grid_degrid_host_steps")
+           "grid_degrid_host_steps", "grid_measure_fma_peak")
 
 
 class GridHostStep(ctypes.Structure):
@@ -102,6 +102,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid_last_error.restype = ctypes.c_char_p
     lib.grid_device_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.grid_device_info.restype = i32
+    lib.grid_measure_fma_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.grid_measure_fma_peak.restype = i32
     lib.grid_tap_form.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.grid_tap_form.restype = i32
     lib.grid_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, i32, i32, i32]

@@ -23,6 +23,36 @@ __global__ void kb_table_kernel(int S, int O, double beta, int fmt, void* out) {
   else ((float*)out)[idx] = (float)val;
 }
 
+// FP32 FMA throughput probe for the roofline denominator: every thread runs
+// kPeakChains independent chains of packed FFMA2 (two FMAs per instruction).
+// The result is stored only when out is not null, so the loop cannot be
+// removed; callers pass null.
+constexpr int kPeakChains = 8;
+__global__ void fma_peak_kernel(int iters, float2 m, float2 c, float2* out) {
+  float2 acc[kPeakChains];
+#pragma unroll
+  for (int k = 0; k < kPeakChains; ++k) acc[k] = make_float2((float)threadIdx.x * 1e-7f + (float)k, (float)k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) acc[k] = __ffma2_rn(acc[k], m, c);
+  }
+  if (out) {
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) s = __fadd2_rn(s, acc[k]);
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+  }
+}
+
+cudaError_t launch_fma_peak(int blocks, int threads, int iters, cudaStream_t st) {
+  fma_peak_kernel<<<blocks, threads, 0, st>>>(iters, make_float2(0.9999f, 0.9999f), make_float2(1e-4f, 1e-4f), nullptr);
+  return cudaGetLastError();
+}
+
+double fma_peak_flops_per_launch(int blocks, int threads, int iters) {
+  return (double)blocks * threads * iters * kPeakChains * 2 /* FMAs per FFMA2 */ * 2 /* flop per FMA */;
+}
+
 // Per-visibility indices exactly as the gridding kernels stage them.
 __global__ void indices_kernel(Args a, int32_t* cell, int32_t* sub) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -814,6 +814,31 @@ int grid_tap_form(int Bu, int Bv, int npol, int* form, int* multiplies) {
   return GRID_OK;
 }
 
+int grid_measure_fma_peak(int iters, double* tflops, cudaStream_t stream) {
+  g_err.clear();
+  if (!tflops || iters < 1 || iters > (1 << 24)) return fail(GRID_ERR_INVALID, "iters=%d must be 1 .. 2^24, tflops not null", iters);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice / attribute");
+  const int threads = 256, blocks = sms * 8;  // 64 warps per SM: every FMA pipe kept busy
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e == cudaSuccess) e = launch_fma_peak(blocks, threads, iters, stream);  // warm-up (clocks up)
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], stream);
+  if (e == cudaSuccess) e = launch_fma_peak(blocks, threads, iters, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "FMA peak measurement");
+  *tflops = fma_peak_flops_per_launch(blocks, threads, iters) / (ms * 1e-3) / 1e12;
+  return GRID_OK;
+}
+
 int grid_device_info(int* sm_count, int* fma_lanes_per_sm, int* max_clock_khz) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -46,6 +46,8 @@ struct TileKernel {
 const TileKernel* find_tile_kernel(int S, int P);
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps);
 
+cudaError_t launch_fma_peak(int blocks, int threads, int iters, cudaStream_t st);
+double fma_peak_flops_per_launch(int blocks, int threads, int iters);
 cudaError_t launch_kb_table(int S, int O, double beta, int fmt, void* out, cudaStream_t st);
 cudaError_t launch_indices(const Args& a, int32_t* cell, int32_t* sub, cudaStream_t st);
 cudaError_t launch_patch_binning(const Args& a, const PatchScratch& ps, cudaStream_t st);

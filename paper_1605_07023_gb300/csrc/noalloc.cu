@@ -3,12 +3,11 @@
 //
 // Who needs it: a real-time imaging pipeline that reserves all of its device
 // memory at start-up and must never call the allocator in steady state (an
-// allocation can stall or fail half way through an observation); code that
-// runs while a stream is being captured into a CUDA graph, where cudaMalloc
-// is not allowed; and a host framework that owns the device heap through its
-// own allocator, so a library allocating behind its back would break its
-// accounting. grid() cannot serve them, because plan creation and the patch
-// schedule's first call allocate scratch with cudaMalloc.
+// allocation can stall or fail half way through an observation), and a host
+// framework that owns the device heap through its own allocator, so a library
+// allocating behind its back would break its accounting. grid() cannot serve
+// them, because plan creation and the patch schedule's first call allocate
+// scratch with cudaMalloc.
 //
 // This entry point takes the plan parameters directly and keeps the patch
 // schedule's binning scratch (patch counts and offsets, per-chunk patch ids,
@@ -55,7 +54,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 // Device address of the scratch, looked up once per device (with that device
 // current) on the first call. The name is only a host-side stand-in; kernels
-// must get this address.
+// must get this address. The cached address belongs to the device's current
+// context: after cudaDeviceReset it is stale, so the entry point must not be
+// used across a reset.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
@@ -91,6 +92,7 @@ int grid_patch_static(int G, int S, int oversample, int npol, int Bu, int Bv, in
   if (S < 1 || S > 64 || S > G) return sfail(GRID_ERR_INVALID, "S must be 1..64 and <= G");
   if (oversample < 1 || oversample > 256 || (oversample & (oversample - 1)))
     return sfail(GRID_ERR_INVALID, "oversample must be a power of two <= 256");
+  if (npol != 1 && npol != 2 && npol != 4) return sfail(GRID_ERR_UNSUPPORTED, "npol must be 1, 2 or 4");
   if (precision < GRID_PREC_F32 || precision > GRID_PREC_F16) return sfail(GRID_ERR_INVALID, "bad precision");
   if (n_vis < 0) return sfail(GRID_ERR_INVALID, "n_vis < 0");
   if (!kernel_table || !grid || ((uintptr_t)grid % 16)) return sfail(GRID_ERR_INVALID, "null kernel_table, or null or misaligned grid");
@@ -98,6 +100,7 @@ int grid_patch_static(int G, int S, int oversample, int npol, int Bu, int Bv, in
   if (!uv || !vis || ((uintptr_t)uv % 16)) return sfail(GRID_ERR_INVALID, "null uv or vis, or misaligned uv");
   const size_t vb = (precision == GRID_PREC_F32 ? 8 : 4) * (size_t)npol;
   if ((uintptr_t)vis % (vb >= 16 ? 16 : vb)) return sfail(GRID_ERR_INVALID, "misaligned vis");
+  if ((uintptr_t)weights % 4) return sfail(GRID_ERR_INVALID, "weights must be 4-byte aligned");
   const long long n_chunks = (n_vis + kStaticChunkLen - 1) / kStaticChunkLen;
   if (n_chunks > kStaticMaxChunks)
     return sfail(GRID_ERR_INVALID, "n_vis above the static-scratch limit of " +

@@ -73,3 +73,23 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_threaded_oracle_matches_the_single_thread_oracle():
+    """The all-core CPU baseline runs the unchanged oracle from several threads (bands of grid rows,
+    slices of visibilities); its grid and degridded values must be the single-thread oracle's up to
+    the order of additions, including footprints that straddle a band edge."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import oracle
+    from paper_1605_07023_gb300 import synth
+    w = synth.plain_single_pol()
+    t = oracle.kb_table(w.S, w.oversample, w.beta)
+    g1, sk1 = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, t)
+    d1, _ = oracle.degrid(w.G, w.S, w.oversample, w.uv, g1, t)
+    for n in (1, 3, 8):
+        g, d, sk, _ = bench.oracle_threads(w, t, n)
+        assert sk == sk1
+        assert np.linalg.norm(g - g1) <= 1e-12 * np.linalg.norm(g1)
+        assert np.linalg.norm(d - d1) <= 1e-12 * np.linalg.norm(d1)
