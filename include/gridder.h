@@ -80,7 +80,8 @@ enum {
   /* Gridding as GRID_SCHED_CHUNKED. Degridding by tile gather: each warp
    * takes 32 consecutive visibilities, copies the bounding box of their
    * footprints (up to (S+13) x (S+13) cells per polarization) from the grid
-   * into shared memory, and each lane sums its own visibility's footprint
+   * into shared memory (bulk asynchronous copies, one per box row and
+   * plane), and each lane sums its own visibility's footprint
    * from there, with no reduction between threads (rows first, the separable
    * form of the Sec. 6 remark). A group whose box is larger reads the grid
    * directly. The same results as the chunked degridder up to FP32 rounding.
@@ -206,12 +207,15 @@ int grid_compute_indices(grid_plan_t plan, int64_t n_vis, const double* uv, int3
 int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
 
 /*
- * Status flags of the plan's gridding calls since it was created or last
- * reset (host call; synchronises with the device word). No passage of the
- * paper defines it: it reports the lazy-box gridder's bounded waits.
- *   bit 0 (GRID_STATUS_COPY_TIMEOUT): a bulk copy of a batch of records into
- *   shared memory did not complete within the kernel's poll limit. The team
- *   then skipped the rest of its chunk, so the grid is incomplete.
+ * Status flags of the plan's calls since it was created or last reset (host
+ * call; synchronises with the device word). No passage of the paper defines
+ * it: it reports the bounded waits of the kernels that copy with the TMA
+ * unit (the lazy-box gridder and the tile degridder).
+ *   bit 0 (GRID_STATUS_COPY_TIMEOUT): a bulk copy into shared memory did not
+ *   complete within the kernel's poll limit. The lazy gridder's team then
+ *   skipped the rest of its chunk (the grid is incomplete); the tile
+ *   degridder's warp wrote wrong values for that group and read the grid
+ *   directly afterwards.
  * reset != 0 zeroes the flags afterwards. flags must not be NULL.
  */
 enum { GRID_STATUS_COPY_TIMEOUT = 1 };

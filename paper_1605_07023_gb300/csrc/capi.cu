@@ -498,6 +498,7 @@ int degrid_weighted(grid_plan_t pl, int64_t n_vis, const double* uv, const void*
   a.table = kernel_table;
   a.grid = (float2*)grid_in;
   a.vis_out = (float2*)vis;
+  a.status = (unsigned*)(pl->d_skipped + 1);
   void* args[] = {&a};
   cudaError_t e;
   if (pl->tile) {

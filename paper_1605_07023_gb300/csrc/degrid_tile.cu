@@ -16,6 +16,10 @@
 // group into two halves with a smaller tile measured slower.) Warps are
 // persistent and load the next group's positions one group ahead.
 //
+// The box reaches shared memory by bulk asynchronous copies (cp.async.bulk,
+// the TMA unit's untiled form): one copy per box row and polarization plane,
+// issued by the warp's lanes, completing on the warp's mbarrier.
+//
 // The index rule, validity, skipped count and output layout are those of the
 // sliding-window degridder.
 #include "kernels.cuh"
@@ -64,15 +68,6 @@ __device__ __forceinline__ void footprint_dot(Ptr base, Stride rstride, Stride p
   }
 }
 
-// A 16-byte global-to-shared copy (two cells) that bypasses L1 and does not
-// wait for its data (cp.async.cg); both addresses are 16-byte aligned.
-// copy_async_wait_all() waits for all of the thread's copies.
-__device__ __forceinline__ void copy_async16(float2* dst, const float2* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void copy_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // The direct path for a group whose box does not fit the tile: kept out
 // of line so that it adds no registers to the tile path.
 template <int S, int P>
@@ -91,7 +86,16 @@ __global__ void degrid_tile_kernel(Args a) {
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = load_tap(a.table, a.tab_fmt, i);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* tile = (float2*)(smem + align16((size_t)ntab * 4)) + (size_t)warp * T::CELLS;
+  // one mbarrier per warp, after all the tiles
+  const uint32_t mbar = smem_addr((float2*)(smem + align16((size_t)ntab * 4)) + (size_t)(blockDim.x >> 5) * T::CELLS) +
+                        8u * warp;
+  if (lane == 0) {
+    mbar_init(mbar);
+    fence_mbar_init();
+  }
   __syncthreads();
+  uint32_t phase = 0;   // parity of the mbarrier's next completion
+  bool failed = false;  // a copy did not complete in time: later groups read the grid directly
 
   const int G = g.G;
   const size_t GG = (size_t)G * G;
@@ -138,23 +142,26 @@ __global__ void degrid_tile_kernel(Args a) {
       const int xe = xmin & ~1;                    // first column of the copy
       const int npair = (xmax + S - xe + 1) >> 1;  // cell pairs per row
       const int sy = ymax - ymin + S;
-      if (2 * npair <= T::TW && sy <= T::TW && xe + 2 * npair <= G) {
-        // Copy with asynchronous 16-byte copies, all of a lane's copies in
-        // flight at once: lanes spread over 32 / npair rows at a time.
-        const int rpp = 32 / npair;
-        const int lr = lane / npair, pc = lane - lr * npair;
-        if (lr < rpp) {
-          int p = 0, row = lr;
-          for (int r = lr; r < P * sy; r += rpp) {
-            while (row >= sy) { row -= sy; ++p; }
-            copy_async16(tile + p * T::PS + row * T::RS + 2 * pc,
-                         a.grid + (size_t)p * GG + (size_t)(ymin + row) * G + (xe + 2 * pc));
-            row += rpp;
-          }
-        }
-        copy_async_wait_all();
+      if (!failed && 2 * npair <= T::TW && sy <= T::TW && xe + 2 * npair <= G) {
+        // One bulk copy per (plane, row) of the box, 16*npair bytes each, spread over the lanes;
+        // the last group's reads of the tile are ordered before these writes (syncwarp, then a
+        // proxy fence in every issuing lane), and lane 0 announces the byte count first.
+        const uint32_t row_bytes = 16u * (uint32_t)npair;
+        if (lane == 0) mbar_expect(mbar, row_bytes * (uint32_t)(P * sy));
         __syncwarp();
-        if (ok) footprint_dot<S, P>((const float2*)tile + (y0 - ymin) * T::RS + (x0 - xe), T::RS, T::PS, tu, tv, s);
+        fence_proxy_async();
+        for (int r = lane; r < P * sy; r += 32) {
+          const int p = r / sy, row = r - p * sy;
+          bulk_load(smem_addr(tile + p * T::PS + row * T::RS),
+                    a.grid + (size_t)p * GG + (size_t)(ymin + row) * G + xe, row_bytes, mbar);
+        }
+        if (!mbar_wait(mbar, phase)) {
+          failed = true;
+          if (lane == 0 && a.status) atomicOr(a.status, 1u);
+        }
+        phase ^= 1u;
+        __syncwarp();
+        if (ok && !failed) footprint_dot<S, P>((const float2*)tile + (y0 - ymin) * T::RS + (x0 - xe), T::RS, T::PS, tu, tv, s);
         __syncwarp();  // the tile is refilled for the next group
       } else if (ok) {
         footprint_dot_global<S, P>((const float2*)a.grid + (size_t)y0 * G + x0, G, tu, tv, s);
@@ -167,6 +174,8 @@ __global__ void degrid_tile_kernel(Args a) {
       for (int p = 0; p < P; ++p) __stcs(out + p, make_float2(s[p].x * w, s[p].y * w));
     }
   }
+  // a copy given up on may still be landing in this CTA's shared memory
+  if (failed) mbar_wait(mbar, phase ^ 1u);
 }
 
 template <int S, int P>
@@ -189,7 +198,7 @@ const TileKernel* find_tile_kernel(int S, int P) {
 }
 
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps) {
-  return align16((size_t)O * t.S * 4) + (size_t)warps * t.cells * sizeof(float2);
+  return align16((size_t)O * t.S * 4) + (size_t)warps * t.cells * sizeof(float2) + (size_t)warps * 8;
 }
 
 }  // namespace gbg

@@ -47,7 +47,6 @@ constexpr unsigned kBoxNone = 0x7FFF7FFFu;   // no box yet
 constexpr unsigned kClampLoNone = 0x80008000u;  // clamp bounds of an invalid record: the box stays
 constexpr unsigned kClampHiNone = 0x7FFF7FFFu;
 constexpr int kOffNone = 0x3FFFFFFF;         // table offset of an invalid record (clamped to the table)
-constexpr int kWaitLimit = 1 << 20;          // mbarrier polls before a batch is given up
 
 template <int B>
 struct Log2B {
@@ -108,31 +107,6 @@ __device__ __forceinline__ void lazy_tables(float2* tabU, float2* tabV, const Ar
     const int k = (mm - g.nv + 1) * BV + j - ph;
     tabV[idx] = splat((k >= 0 && k < g.S) ? load_tap(a.table, a.tab_fmt, r * g.S + k) : 0.f);
   }
-}
-
-// --- bulk asynchronous copies and mbarriers (shared-memory addresses are 32-bit)
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
-// Polls the mbarrier's phase `parity` at most kWaitLimit times (each poll may
-// suspend the thread for a while); false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
-    if (ok) return true;
-  }
-  return false;
 }
 
 // Bytes of one record's values in the input format.
@@ -274,7 +248,7 @@ __global__ void grid_lazy_kernel(Args a) {
   if (l == 0) {
     mbar_init(mbar0);
     mbar_init(mbar1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_mbar_init();
   }
   lazy_tables<BU, BV>(tabU, tabV, a);
   __syncthreads();  // tables and mbarriers ready
@@ -317,7 +291,7 @@ __global__ void grid_lazy_kernel(Args a) {
     const long long kn = kb + kRBL;
     if (!failed && bt + 1 < nb && lazy_bulk_ok(a, kn, vend, vb)) {
       if (l == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_proxy_async();
         lazy_issue(a, kn, b ? raw0 : raw1, b ? mbar0 : mbar1, vb);
       }
       pending |= 1u << (b ^ 1);

@@ -70,6 +70,7 @@ def check(gb, w, threads=0, weights=None, seed=0, precision="f32"):
         ref = ref * weights[:, None]
     got = out.cpu().numpy()
     assert plan.skipped() == skipped
+    assert plan.status() == 0  # every bulk copy of a box completed
     for p in range(w.npol):
         e = rel_l2(got[:, p], ref[:, p])
         assert e <= TOL, (w.name, p, e)
