@@ -353,9 +353,12 @@ int grid_batch_create(grid_batch_t* out, int G, int oversample, int npol, int Bu
 /*
  * As grid_batch_create(), with two block shapes: items with S >= S_split use
  * (Bu2, Bv2), the others (Bu, Bv). Larger supports favour larger blocks
- * (Sec. 5: the best coarsening depends on the bin size). Built pairs: npol 1
- * with (2,2)+(4,2) or (2,2)+(4,4), npol 4 with (2,2)+(4,2); (Bu2, Bv2) equal
- * to (Bu, Bv) gives the one-shape kernel. S_split in 0..64 (0: one shape).
+ * (Sec. 5: the best coarsening depends on the bin size). Each shape has its
+ * own persistent launch (back to back on the stream), compiled for that shape
+ * alone, so either may be any built one-shape kernel: npol 1 with (1,1),
+ * (2,1), (1,2), (2,2), (3,3), (4,2), (2,4), (4,4); npol 4 with (1,1), (2,1),
+ * (2,2), (4,2). (Bu2, Bv2) equal to (Bu, Bv) gives one launch. S_split in
+ * 0..64 (0: one shape).
  */
 int grid_batch_create_ex(grid_batch_t* out, int G, int oversample, int npol, int Bu, int Bv, int Bu2, int Bv2,
                          int S_split, int max_S, int precision, int vis_per_chunk, int threads);

@@ -362,8 +362,8 @@ class BatchPlan:
 
     items: list of dicts with keys uv, vis, weights (or None), table, grid, S,
     all CUDA tensors (see grid()). Tensors must stay alive while the batch is
-    executed. execute() enqueues one kernel on the current stream and can be
-    captured in a CUDA graph.
+    executed. execute() enqueues one kernel per block shape on the current
+    stream and can be captured in a CUDA graph.
     """
 
     def __init__(self, G: int, oversample: int, npol: int, Bu: int = 2, Bv: int = 2, max_S: int = 15,

@@ -192,7 +192,8 @@ def tune(G: int, S: int, oversample: int, npol: int, precision: str = "f32", n_v
 # Batched gridding: one-shape kernels and the two-shape pairs the library builds
 BATCH_SHAPES = {1: [(1, 1), (2, 1), (1, 2), (2, 2), (3, 3), (4, 2), (2, 4), (4, 4)],
                 4: [(1, 1), (2, 1), (2, 2), (4, 2)]}
-BATCH_PAIRS = {1: [((2, 2), (4, 2)), ((2, 2), (4, 4))], 4: [((2, 2), (4, 2))]}
+BATCH_PAIRS = {1: [((2, 2), (4, 2)), ((2, 2), (2, 4)), ((2, 2), (4, 4)), ((2, 1), (2, 2)), ((2, 1), (4, 2))],
+               4: [((2, 2), (4, 2)), ((2, 1), (2, 2))]}
 BATCH_SPLITS = (9, 11, 13)
 
 

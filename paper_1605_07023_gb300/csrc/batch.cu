@@ -1,8 +1,11 @@
 // Batched gridding: the C ABI (grid_batch_*) and its kernel instantiations.
 // Many grids of the same size, with uneven visibility counts and per-grid
-// GCF support, are gridded by one persistent kernel launch. The launch can
-// be captured in a CUDA graph because grid_batch_execute() allocates nothing
-// and only enqueues a counter reset and one kernel.
+// GCF support, are gridded by persistent kernel launches: one launch per
+// block shape (items with S >= S_split may use a second shape, Sec. 5: the
+// best coarsening depends on the bin size), each compiled for its own shape
+// so that the larger shape's registers do not bind the smaller one. The
+// launches can be captured in a CUDA graph because grid_batch_execute()
+// allocates nothing and only enqueues a counter reset and the kernels.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -17,29 +20,32 @@ namespace gbg {
 
 #define GB_BATCH(BU, BV, P) \
   {BU, BV, BU, BV, P, (const void*)&grid_batch_kernel<BU, BV, BU, BV, P>, &batch_smem_bytes<BU, BV, BU, BV, P>}
-#define GB_BATCH2(BU, BV, BU2, BV2, P) \
-  {BU, BV, BU2, BV2, P, (const void*)&grid_batch_kernel<BU, BV, BU2, BV2, P>, &batch_smem_bytes<BU, BV, BU2, BV2, P>}
 
 static const BatchKernelEntry kBatchKernels[] = {
     GB_BATCH(1, 1, 1), GB_BATCH(2, 1, 1), GB_BATCH(1, 2, 1), GB_BATCH(2, 2, 1), GB_BATCH(3, 3, 1), GB_BATCH(4, 2, 1),
     GB_BATCH(2, 4, 1), GB_BATCH(4, 4, 1), GB_BATCH(1, 1, 4), GB_BATCH(2, 1, 4), GB_BATCH(2, 2, 4), GB_BATCH(4, 2, 4),
-    // two shapes: small supports with 2x2 blocks, large ones with 4x2 (or 4x4)
-    GB_BATCH2(2, 2, 4, 2, 1), GB_BATCH2(2, 2, 4, 4, 1), GB_BATCH2(2, 2, 4, 2, 4),
 };
 
 }  // namespace gbg
 
+// One block shape of a batch: its kernel and launch shape.
+struct BatchShape {
+  const BatchKernelEntry* k = nullptr;
+  int bu = 0, bv = 0;
+  int threads = 0, nb_max = 0, tpc_max = 0, occ = 0;
+  size_t smem = 0;
+  int first_unit = 0, n_units = 0;  // this shape's work units in d_units
+};
+
 struct grid_batch_s {
-  int G, O, P, Bu, Bv, Bu2, Bv2, S_split, max_S, precision, chunk_len, threads, device;
-  int nb_max, tpc_max;
-  const BatchKernelEntry* k;
-  size_t smem;
-  int occ;
+  int G, O, P, S_split, max_S, precision, chunk_len, device;
+  int n_shapes;  // 1, or 2 when items with S >= S_split use the second shape
+  BatchShape shape[2];
   int sm_count;
   // device state
   BatchItem* d_items = nullptr;
   int4* d_units = nullptr;
-  int* d_next = nullptr;
+  int* d_next = nullptr;  // one work counter per shape
   unsigned long long* d_skipped = nullptr;
   int n_items = 0, n_units = 0, cap_items = 0, cap_units = 0;
 };
@@ -51,6 +57,41 @@ int bfail(int code, const char* msg) {
   return code;
 }
 int nb_of(int S, int B) { return ((S + B - 1 + B - 1) / B) * B; }
+
+// Kernel, CTA size, record buffers and residency of one shape for supports up to max_S.
+const BatchKernelEntry* find_batch_kernel(int bu, int bv, int P) {
+  for (const auto& e : kBatchKernels)
+    if (e.bu == bu && e.bv == bv && e.bu2 == bu && e.bv2 == bv && e.p == P) return &e;
+  return nullptr;
+}
+
+int setup_shape(BatchShape& sh, int bu, int bv, int P, int O, int max_S, int threads, const cudaDeviceProp& prop) {
+  sh.k = find_batch_kernel(bu, bv, P);
+  if (!sh.k) return bfail(GRID_ERR_UNSUPPORTED, "no batched kernel built for this block shape and npol");
+  sh.bu = bu;
+  sh.bv = bv;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, sh.k->fn);
+  if (e != cudaSuccess) return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
+  sh.nb_max = std::max(nb_of(max_S, bu), nb_of(max_S, bv));
+  const int ts_max = (nb_of(max_S, bu) / bu) * (nb_of(max_S, bv) / bv);
+  int thr = threads ? threads : 256;
+  thr = std::max(thr, ts_max);
+  thr = std::min(thr, fa.maxThreadsPerBlock);
+  if (ts_max > thr) return bfail(GRID_ERR_UNSUPPORTED, "largest team does not fit in a CTA");
+  sh.threads = thr;
+  // record buffers for at most 32 teams per CTA (small-S items use part of the CTA)
+  const int ts_min = (nb_of(1, bu) / bu) * (nb_of(1, bv) / bv);
+  sh.tpc_max = std::min(32, thr / ts_min);
+  sh.smem = sh.k->smem(O, sh.nb_max, sh.tpc_max);
+  const size_t smem_max = prop.sharedMemPerBlockOptin;
+  if (sh.smem + fa.sharedSizeBytes > smem_max) return bfail(GRID_ERR_UNSUPPORTED, "batched kernel needs too much shared memory");
+  e = cudaFuncSetAttribute(sh.k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa.sharedSizeBytes));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sh.occ, sh.k->fn, sh.threads, sh.smem);
+  if (e == cudaSuccess && sh.occ < 1) e = cudaErrorInvalidConfiguration;
+  if (e != cudaSuccess) return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
+  return GRID_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -75,49 +116,29 @@ int grid_batch_create_ex(grid_batch_t* out, int G, int oversample, int npol, int
     return bfail(GRID_ERR_INVALID, "bad vis_per_chunk or threads");
   if (Bu2 == Bu && Bv2 == Bv) S_split = 0;
   if (S_split < 0 || S_split > 64) return bfail(GRID_ERR_INVALID, "S_split must be 0..64");
-  const BatchKernelEntry* k = nullptr;
-  for (const auto& e : kBatchKernels)
-    if (e.bu == Bu && e.bv == Bv && e.bu2 == Bu2 && e.bv2 == Bv2 && e.p == npol) k = &e;
-  if (!k) return bfail(GRID_ERR_UNSUPPORTED, "no batched kernel built for these block shapes and npol");
+  if (!find_batch_kernel(Bu, Bv, npol) || !find_batch_kernel(Bu2, Bv2, npol))
+    return bfail(GRID_ERR_UNSUPPORTED, "no batched kernel built for these block shapes and npol");
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
   grid_batch_s* b = new grid_batch_s;
-  b->G = G; b->O = oversample; b->P = npol; b->Bu = Bu; b->Bv = Bv; b->Bu2 = Bu2; b->Bv2 = Bv2; b->S_split = S_split;
+  b->G = G; b->O = oversample; b->P = npol; b->S_split = S_split;
   b->max_S = max_S; b->precision = precision;
   b->chunk_len = vis_per_chunk ? vis_per_chunk : 256;
-  b->k = k;
-  cudaError_t e = cudaGetDevice(&b->device);
-  cudaDeviceProp prop;
-  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, b->device);
-  cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k->fn);
-  if (e != cudaSuccess) {
-    delete b;
-    return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
-  }
+  b->device = dev;
   b->sm_count = prop.multiProcessorCount;
-  b->nb_max = std::max(std::max(nb_of(max_S, Bu), nb_of(max_S, Bv)), std::max(nb_of(max_S, Bu2), nb_of(max_S, Bv2)));
-  const int ts_max = std::max((nb_of(max_S, Bu) / Bu) * (nb_of(max_S, Bv) / Bv),
-                              (nb_of(max_S, Bu2) / Bu2) * (nb_of(max_S, Bv2) / Bv2));
-  int thr = threads ? threads : 256;
-  thr = std::max(thr, ts_max);
-  thr = std::min(thr, fa.maxThreadsPerBlock);
-  if (ts_max > thr) {
+  b->n_shapes = S_split > 0 ? 2 : 1;
+  // the first shape serves supports below S_split, the second the rest (up to max_S)
+  int rc = setup_shape(b->shape[0], Bu, Bv, npol, oversample, S_split > 0 ? std::min(max_S, S_split - 1) : max_S,
+                       threads, prop);
+  if (rc == GRID_OK && b->n_shapes == 2) rc = setup_shape(b->shape[1], Bu2, Bv2, npol, oversample, max_S, threads, prop);
+  if (rc != GRID_OK) {
     delete b;
-    return bfail(GRID_ERR_UNSUPPORTED, "largest team does not fit in a CTA");
+    return rc;
   }
-  b->threads = thr;
-  // record buffers for at most 32 teams per CTA (small-S items use part of the CTA)
-  const int ts_min = std::min((nb_of(1, Bu) / Bu) * (nb_of(1, Bv) / Bv), (nb_of(1, Bu2) / Bu2) * (nb_of(1, Bv2) / Bv2));
-  b->tpc_max = std::min(32, thr / ts_min);
-  b->smem = k->smem(oversample, b->nb_max, b->tpc_max);
-  const size_t smem_max = prop.sharedMemPerBlockOptin;
-  if (b->smem + fa.sharedSizeBytes > smem_max) {
-    delete b;
-    return bfail(GRID_ERR_UNSUPPORTED, "batched kernel needs too much shared memory");
-  }
-  e = cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa.sharedSizeBytes));
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->occ, k->fn, b->threads, b->smem);
-  if (e == cudaSuccess && b->occ < 1) e = cudaErrorInvalidConfiguration;
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(int));
+  e = cudaMalloc(&b->d_next, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_skipped, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(b->d_skipped, 0, sizeof(unsigned long long));
   if (e != cudaSuccess) {
@@ -144,7 +165,7 @@ int grid_batch_set(grid_batch_t b, int n_items, const grid_batch_item* items) {
   if (!b || n_items < 0 || (n_items > 0 && !items)) return bfail(GRID_ERR_INVALID, "bad arguments");
   std::vector<BatchItem> hi(n_items);
   struct U { int item; int first; int n; double cost; };
-  std::vector<U> units;
+  std::vector<U> units[2];
   for (int i = 0; i < n_items; ++i) {
     const grid_batch_item& s = items[i];
     if (s.n_vis < 0 || s.S < 1 || s.S > b->max_S) return bfail(GRID_ERR_INVALID, "item S out of range or negative n_vis");
@@ -154,24 +175,28 @@ int grid_batch_set(grid_batch_t b, int n_items, const grid_batch_item* items) {
       return bfail(GRID_ERR_INVALID, "misaligned item pointer");
     const size_t vb = (b->precision == GRID_PREC_F32 ? 8 : 4) * (size_t)b->P;
     if ((uintptr_t)s.vis % (vb >= 16 ? 16 : vb)) return bfail(GRID_ERR_INVALID, "misaligned vis pointer");
-    const int shape = (b->S_split > 0 && s.S >= b->S_split) ? 1 : 0;
-    hi[i] = BatchItem{(const double2*)s.uv, s.vis, s.weights, s.kernel_table, (float2*)s.grid, (long long)s.n_vis, s.S, shape};
-    const int bu = shape ? b->Bu2 : b->Bu, bv = shape ? b->Bv2 : b->Bv;
-    const int nbu = nb_of(s.S, bu), nbv = nb_of(s.S, bv);
-    const int ts = (nbu / bu) * (nbv / bv);
-    const int tpc = std::min(b->tpc_max, b->threads / ts);
+    const int cls = (b->n_shapes == 2 && s.S >= b->S_split) ? 1 : 0;
+    const BatchShape& sh = b->shape[cls];
+    hi[i] = BatchItem{(const double2*)s.uv, s.vis, s.weights, s.kernel_table, (float2*)s.grid, (long long)s.n_vis, s.S, 0};
+    const int nbu = nb_of(s.S, sh.bu), nbv = nb_of(s.S, sh.bv);
+    const int ts = (nbu / sh.bu) * (nbv / sh.bv);
+    const int tpc = std::min(sh.tpc_max, sh.threads / ts);
     const long long nch = (s.n_vis + b->chunk_len - 1) / b->chunk_len;
+    if (nch > 0x7FFFFFFFLL) return bfail(GRID_ERR_INVALID, "item too large");
     for (long long c = 0; c < nch; c += tpc) {
       const int n = (int)std::min<long long>(tpc, nch - c);
       const long long nv = std::min<long long>((long long)n * b->chunk_len, s.n_vis - c * b->chunk_len);
-      units.push_back(U{i, (int)c, n, (double)nv * nbu * nbv});
+      units[cls].push_back(U{i, (int)c, n, (double)nv * nbu * nbv});
     }
-    if (nch > 0x7FFFFFFFLL) return bfail(GRID_ERR_INVALID, "item too large");
   }
-  // most expensive units first (longest-processing-time order for the persistent CTAs)
-  std::stable_sort(units.begin(), units.end(), [](const U& x, const U& y) { return x.cost > y.cost; });
-  std::vector<int4> hu(units.size());
-  for (size_t i = 0; i < units.size(); ++i) hu[i] = make_int4(units[i].item, units[i].first, units[i].n, 0);
+  // per shape, most expensive units first (longest-processing-time order for the persistent CTAs)
+  std::vector<int4> hu;
+  for (int k = 0; k < b->n_shapes; ++k) {
+    std::stable_sort(units[k].begin(), units[k].end(), [](const U& x, const U& y) { return x.cost > y.cost; });
+    b->shape[k].first_unit = (int)hu.size();
+    b->shape[k].n_units = (int)units[k].size();
+    for (const U& u : units[k]) hu.push_back(make_int4(u.item, u.first, u.n, 0));
+  }
   cudaError_t e = cudaSuccess;
   if (n_items > b->cap_items) {
     cudaFree(b->d_items);
@@ -197,19 +222,26 @@ int grid_batch_execute(grid_batch_t b, cudaStream_t stream) {
   b_err.clear();
   if (!b) return bfail(GRID_ERR_INVALID, "null batch");
   if (b->n_units == 0) return GRID_OK;
-  cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(int), stream);
+  cudaError_t e = cudaMemsetAsync(b->d_next, 0, 2 * sizeof(int), stream);
   if (e != cudaSuccess) return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
-  BatchArgs a;
-  memset(&a, 0, sizeof a);
-  a.G = b->G; a.O = b->O;
-  a.log2O = 0;
-  while ((1 << a.log2O) < b->O) ++a.log2O;
-  a.P = b->P; a.fmt = b->precision; a.chunk_len = b->chunk_len; a.nb_max = b->nb_max; a.tpc_max = b->tpc_max;
-  a.items = b->d_items; a.units = b->d_units; a.n_units = b->n_units; a.unit_next = b->d_next; a.skipped = b->d_skipped;
-  const int blocks = std::min(b->sm_count * b->occ, b->n_units);
-  void* args[] = {&a};
-  e = cudaLaunchKernel(b->k->fn, dim3(blocks), dim3(b->threads), args, b->smem, stream);
-  if (e != cudaSuccess) return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
+  // one launch per shape, back to back on the stream (the second kernel's CTAs start as the
+  // first kernel's finish)
+  for (int k = 0; k < b->n_shapes; ++k) {
+    const BatchShape& sh = b->shape[k];
+    if (sh.n_units == 0) continue;
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    a.G = b->G; a.O = b->O;
+    a.log2O = 0;
+    while ((1 << a.log2O) < b->O) ++a.log2O;
+    a.P = b->P; a.fmt = b->precision; a.chunk_len = b->chunk_len; a.nb_max = sh.nb_max; a.tpc_max = sh.tpc_max;
+    a.items = b->d_items; a.units = b->d_units + sh.first_unit; a.n_units = sh.n_units; a.unit_next = b->d_next + k;
+    a.skipped = b->d_skipped;
+    const int blocks = std::min(b->sm_count * sh.occ, sh.n_units);
+    void* args[] = {&a};
+    e = cudaLaunchKernel(sh.k->fn, dim3(blocks), dim3(sh.threads), args, sh.smem, stream);
+    if (e != cudaSuccess) return bfail(GRID_ERR_CUDA, cudaGetErrorString(e));
+  }
   return GRID_OK;
 }
 
@@ -225,9 +257,13 @@ int grid_batch_skipped(grid_batch_t b, int64_t* n_skipped, int reset) {
 
 int grid_batch_describe(grid_batch_t b, int* threads, int* n_units, int* ctas) {
   if (!b) return bfail(GRID_ERR_INVALID, "null batch");
-  if (threads) *threads = b->threads;
+  if (threads) *threads = b->shape[0].threads;
   if (n_units) *n_units = b->n_units;
-  if (ctas) *ctas = std::min(b->sm_count * b->occ, b->n_units);
+  if (ctas) {
+    int c = 0;
+    for (int k = 0; k < b->n_shapes; ++k) c += std::min(b->sm_count * b->shape[k].occ, b->shape[k].n_units);
+    *ctas = c;
+  }
   return GRID_OK;
 }
 

@@ -32,7 +32,7 @@ def device_items(ws):
         t64 = oracle.kb_table(w.S, w.oversample, w.beta).astype(np.float32)
         items.append(dict(uv=torch.from_numpy(w.uv).cuda(), vis=torch.from_numpy(w.vis).cuda(),
                           weights=torch.from_numpy(w.weights).cuda(), table=torch.from_numpy(t64).cuda(),
-                          grid=torch.zeros((1, w.G, w.G), dtype=torch.complex64, device="cuda"), S=w.S))
+                          grid=torch.zeros((w.npol, w.G, w.G), dtype=torch.complex64, device="cuda"), S=w.S))
     return items
 
 
@@ -50,7 +50,8 @@ def test_batch_matches_oracle(gb, B):
     assert bp.skipped() == 0
 
 
-@pytest.mark.parametrize("shapes", [((2, 2), (4, 2), 13), ((2, 2), (4, 4), 11)])
+@pytest.mark.parametrize("shapes", [((2, 2), (4, 2), 13), ((2, 2), (4, 4), 11), ((2, 1), (2, 2), 9),
+                                    ((2, 2), (2, 4), 11), ((1, 1), (3, 3), 10), ((4, 4), (2, 2), 9)])
 def test_batch_two_shapes_matches_oracle(gb, shapes):
     (bu, bv), (bu2, bv2), split = shapes
     ws = [w for row in small_batch(n_chan=2, total=400_000, seed=4) for w in row]
@@ -65,10 +66,13 @@ def test_batch_two_shapes_matches_oracle(gb, shapes):
         assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, (w.name, shapes)
 
 
-def test_batch_cuda_graph_replay(gb):
+@pytest.mark.parametrize("two", [False, True])
+def test_batch_cuda_graph_replay(gb, two):
+    """Replay of a captured batch: one launch, or one launch per block shape."""
     ws = [w for row in small_batch(n_chan=2, total=300_000, seed=1) for w in row]
     items = device_items(ws)
-    bp = gb.BatchPlan(1024, 8, 1, Bu=2, Bv=2, max_S=15)
+    shapes = dict(Bu2=4, Bv2=2, S_split=11) if two else {}
+    bp = gb.BatchPlan(1024, 8, 1, Bu=2, Bv=2, max_S=15, **shapes)
     bp.set(items)
     bp.execute()                    # warm up outside the capture
     torch.cuda.synchronize()
@@ -140,3 +144,23 @@ def test_full_batching_workload(gb):
     for w, it in zip(ws, items):
         ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
         assert rel_l2(it["grid"].cpu().numpy()[0], ref[0]) <= 1e-5, w.name
+
+
+def test_batch_two_shapes_quad_pol(gb):
+    """Four polarizations, two shapes (2x1 below S=9, 2x2 above)."""
+    rng = np.random.default_rng(8)
+    ws = []
+    for k, S in enumerate((7, 7, 9, 11)):
+        w = synth.scaled_down(synth.quad_pol(seed=k), 20_000 + 777 * k)
+        ws.append(synth.Workload(f"qp{k}", w.G, S, w.oversample, 4, w.uv * 0.9, w.vis, rng.uniform(0.5, 2, w.n_vis).astype(np.float32),
+                                 beta=2.34 * S))
+    items = device_items(ws)
+    bp = gb.BatchPlan(2048, 8, 4, Bu=2, Bv=1, Bu2=2, Bv2=2, S_split=9, max_S=11)
+    bp.set(items)
+    bp.execute()
+    torch.cuda.synchronize()
+    for w, it in zip(ws, items):
+        ref, _ = oracle.grid(w.G, w.S, w.oversample, w.uv, w.vis, w.weights, it["table"].cpu().numpy().astype(np.float64))
+        got = it["grid"].cpu().numpy()
+        for p in range(4):
+            assert rel_l2(got[p], ref[p]) <= 1e-5, (w.name, p)
