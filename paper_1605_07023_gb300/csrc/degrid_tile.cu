@@ -150,10 +150,12 @@ __global__ void degrid_tile_kernel(Args a) {
         if (lane == 0) mbar_expect(mbar, row_bytes * (uint32_t)(P * sy));
         __syncwarp();
         fence_proxy_async();
-        for (int r = lane; r < P * sy; r += 32) {
-          const int p = r / sy, row = r - p * sy;
-          bulk_load(smem_addr(tile + p * T::PS + row * T::RS),
-                    a.grid + (size_t)p * GG + (size_t)(ymin + row) * G + xe, row_bytes, mbar);
+        // lane r copies row r of every plane (sy <= TW rows; no division)
+        for (int row = lane; row < sy; row += 32) {
+          const float2* src = a.grid + (size_t)(ymin + row) * G + xe;
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+            bulk_load(smem_addr(tile + p * T::PS + row * T::RS), src + (size_t)p * GG, row_bytes, mbar);
         }
         if (!mbar_wait(mbar, phase)) {
           failed = true;
