@@ -69,7 +69,10 @@ enum { GRID_PREC_F32 = 0, GRID_PREC_BF16 = 1, GRID_PREC_F16 = 2 };
 enum {
   /* Sec. 4: fixed-size chunks of baseline-ordered visibilities, one team of
    * threads per chunk. Flushes go straight to the grid in global memory with
-   * atomic adds. */
+   * atomic adds. Where the team has at most 64 threads, each staged batch of
+   * 32 visibilities is processed in the order of its footprints' first block
+   * (v, then u) rather than the input order, which groups the visibilities
+   * that share a box; the grid is the same up to FP32 summation order. */
   GRID_SCHED_CHUNKED = 0,
   /* The same chunks, first binned by the grid "patch" (a square region of
    * the grid) their footprints start in. A CTA accumulates one patch plus a
@@ -220,6 +223,15 @@ int grid_plan_skipped(grid_plan_t plan, int64_t* n_skipped, int reset);
  */
 enum { GRID_STATUS_COPY_TIMEOUT = 1 };
 int grid_plan_status(grid_plan_t plan, unsigned* flags, int reset);
+
+/*
+ * Name of the kernel grid() launches for this plan (host call, no device
+ * work): "rotated" (the chunked schedule with phase-rotated tap tables and
+ * box-ordered batches, teams of at most 32 threads), "rotated-wide" (the
+ * same, 33..64 threads), "chunked" (larger teams), "patch" or "lazy". The
+ * string is static; NULL plan gives "".
+ */
+const char* grid_plan_gridder(grid_plan_t plan);
 
 /*
  * Compression (Sec. 2.2, last paragraph, after Muscat): adjacent visibilities

@@ -95,8 +95,12 @@ class Plan:
         _lib.check(_lib.load().grid_plan_describe(self.handle, ctypes.byref(d), ctypes.byref(bu), ctypes.byref(bv),
                                                   ctypes.byref(ts)))
         out = {n: getattr(d, n) for n, _ in _lib.GridPlanDesc._fields_}
-        out.update(bin_u=bu.value, bin_v=bv.value, team_size=ts.value)
+        out.update(bin_u=bu.value, bin_v=bv.value, team_size=ts.value, gridder=self.gridder())
         return out
+
+    def gridder(self) -> str:
+        """Name of the kernel grid() launches: rotated, rotated-wide, chunked, patch or lazy."""
+        return _lib.load().grid_plan_gridder(self.handle).decode()
 
     def skipped(self, reset: bool = False) -> int:
         v = ctypes.c_int64()

@@ -21,7 +21,7 @@ PREC = {"f32": 0, "bf16": 1, "f16": 2}
 SCHED = {"chunked": 0, "patch": 1, "tile": 2, "lazy": 3}
 
 EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
-           "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped", "grid_plan_status",
+           "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped", "grid_plan_status", "grid_plan_gridder",
            "grid_last_error", "grid_device_info", "grid_tap_form", "grid_batch_create", "grid_batch_set", "grid_batch_execute",
            "grid_batch_skipped", "grid_batch_describe", "grid_batch_destroy", "grid_batch_last_error",
            "grid_patch_static", "grid_patch_static_last_error", "grid_compress", "degrid_expand", "grid_degrid_host", "grid_batch_create_ex",
@@ -89,6 +89,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.grid_plan_skipped.restype = i32
     lib.grid_plan_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint), i32]
     lib.grid_plan_status.restype = i32
+    lib.grid_plan_gridder.argtypes = [vp]
+    lib.grid_plan_gridder.restype = ctypes.c_char_p
     lib.grid_compress.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.grid_compress.restype = i32
     lib.degrid_expand.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp]

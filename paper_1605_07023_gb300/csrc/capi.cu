@@ -28,6 +28,10 @@ struct grid_plan_s {
   int tile_threads;
   size_t tile_smem;
   int occ_tile;            // resident tile-degridding CTAs per SM
+  const void* rot_fn;      // chunked schedule with rotated tables (teams of at most 64 threads), else null
+  int rot_tpc;             // its teams per CTA
+  int rot_threads;
+  size_t rot_smem;
   const LazyEntry* lazy;   // lazy-box schedule: the gridding kernel, its geometry and launch shape
   Geometry gl;             // the widened bin (nu, nv, ts) of the lazy gridder
   int lazy_threads;
@@ -70,6 +74,14 @@ size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 const LazyEntry* find_lazy_kernel(int bu, int bv, int p) {
   int n = 0;
   const LazyEntry* t = p == 1 ? lazy_kernels_p1(&n) : p == 2 ? lazy_kernels_p2(&n) : p == 4 ? lazy_kernels_p4(&n) : nullptr;
+  for (int i = 0; t && i < n; ++i)
+    if (t[i].bu == bu && t[i].bv == bv) return &t[i];
+  return nullptr;
+}
+
+const RotEntry* find_rot_kernel(int bu, int bv, int p) {
+  int n = 0;
+  const RotEntry* t = p == 1 ? rot_kernels_p1(&n) : p == 2 ? rot_kernels_p2(&n) : p == 4 ? rot_kernels_p4(&n) : nullptr;
   for (int i = 0; t && i < n; ++i)
     if (t[i].bu == bu && t[i].bv == bv) return &t[i];
   return nullptr;
@@ -358,6 +370,8 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     gl.nvB = gl.nbv;
     gl.mu = (unsigned)((1ull << 31) / (unsigned)gl.nu + 1);
     gl.mv = (unsigned)((1ull << 31) / (unsigned)gl.nv + 1);
+    gl.mbu = (unsigned)((1ull << 31) / (unsigned)gl.nbu + 1);
+    gl.mbv = (unsigned)((1ull << 31) / (unsigned)gl.nbv + 1);
     if (gl.ts > 32) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "lazy schedule: %d threads per team (more than a warp)", gl.ts); }
     int seg = 1;
     while (seg < gl.ts) seg <<= 1;
@@ -380,6 +394,32 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     pl->lazy_threads = warps * 32;
     pl->lazy_teams = gl.tpc;
     pl->lazy_smem = sm;
+  }
+  if (d.schedule == GRID_SCHED_CHUNKED || d.schedule == GRID_SCHED_TILE) {
+    // the chunked schedule grids with the rotated-table kernel wherever it applies: teams of at
+    // most 64 threads whose CTA fits in shared memory; otherwise with grid_kernel
+    const RotEntry* re = find_rot_kernel(kbu, kbv, d.npol);
+    if (re && g.ts <= 64) {
+      const void* fn = g.ts <= 32 ? re->fn : re->fn_wide;
+      cudaFuncAttributes fa_r;
+      e = cudaFuncGetAttributes(&fa_r, fn);
+      if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncGetAttributes (rotated)"); }
+      Geometry gr = g;
+      const int target = d.threads > 0 ? d.threads : 256;
+      gr.tpc = target / g.ts;
+      if (gr.tpc < 1) gr.tpc = 1;
+      while (gr.tpc > 1 && gr.tpc * g.ts > fa_r.maxThreadsPerBlock) --gr.tpc;
+      size_t (*const smem_of)(const Geometry&) = g.ts <= 32 ? re->smem : re->smem_wide;
+      while (gr.tpc > 1 && smem_of(gr) + fa_r.sharedSizeBytes > smem_max) --gr.tpc;
+      if (g.ts <= fa_r.maxThreadsPerBlock && smem_of(gr) + fa_r.sharedSizeBytes <= smem_max) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem_max - fa_r.sharedSizeBytes));
+        if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncSetAttribute (rotated)"); }
+        pl->rot_fn = fn;
+        pl->rot_tpc = gr.tpc;
+        pl->rot_threads = gr.tpc * g.ts;
+        pl->rot_smem = smem_of(gr);
+      }
+    }
   }
   // word 0: skipped visibilities; word 1: status flags of the lazy gridder
   e = cudaMalloc(&pl->d_skipped, 2 * sizeof(unsigned long long));
@@ -446,6 +486,15 @@ int grid(grid_plan_t pl, int64_t n_vis, const double* uv, const void* vis, const
     void* args[] = {&a};
     e = cudaLaunchKernel(pl->lazy->fn, dim3((unsigned)blocks), dim3(pl->lazy_threads), args, pl->lazy_smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "grid (lazy) kernel launch");
+    return GRID_OK;
+  }
+  if (pl->rot_fn) {
+    a.g.tpc = pl->rot_tpc;
+    const long long blocks = (a.n_chunks + pl->rot_tpc - 1) / pl->rot_tpc;
+    if (blocks > 0x7FFFFFFFLL) return fail(GRID_ERR_INVALID, "too many chunks");
+    void* args[] = {&a};
+    e = cudaLaunchKernel(pl->rot_fn, dim3((unsigned)blocks), dim3(pl->rot_threads), args, pl->rot_smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid (rotated) kernel launch");
     return GRID_OK;
   }
   if (pl->desc.schedule != GRID_SCHED_PATCH) {
@@ -554,6 +603,13 @@ int grid_plan_skipped(grid_plan_t pl, int64_t* n_skipped, int reset) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
   }
   return GRID_OK;
+}
+
+const char* grid_plan_gridder(grid_plan_t pl) {
+  if (!pl) return "";
+  if (pl->lazy) return "lazy";
+  if (pl->rot_fn) return pl->g.ts <= 32 ? "rotated" : "rotated-wide";
+  return pl->desc.schedule == GRID_SCHED_PATCH ? "patch" : "chunked";
 }
 
 int grid_plan_status(grid_plan_t pl, unsigned* flags, int reset) {

@@ -6,6 +6,7 @@
 
 #include "kernels.cuh"
 #include "lazy.cuh"
+#include "rotated.cuh"
 
 namespace gbg {
 
@@ -31,6 +32,11 @@ struct PatchScratch {
 const KernelEntry* kernels_p1(int* n);
 const KernelEntry* kernels_p2(int* n);
 const KernelEntry* kernels_p4(int* n);
+
+// Rotated-table chunked gridders (inst_rot_p*.cu), one entry per (Bu, Bv).
+const RotEntry* rot_kernels_p1(int* n);
+const RotEntry* rot_kernels_p2(int* n);
+const RotEntry* rot_kernels_p4(int* n);
 
 // Lazy-box gridders (inst_lazy_p*.cu), one per (Bu, Bv, P) that is built.
 const LazyEntry* lazy_kernels_p1(int* n);

@@ -50,6 +50,7 @@ struct Geometry {
   int tpc;        // teams per CTA
   int nuB, nvB;   // nu*Bu, nv*Bv: a bin's width in table entries
   unsigned mu, mv;  // floor(2^31/nu) + 1, floor(2^31/nv) + 1: exact division of block indices < 2^15
+  unsigned mbu, mbv;  // floor(2^31/nbu) + 1, floor(2^31/nbv) + 1: exact cell index mod bin width
 };
 
 // Bin and team shape for blocks of Bu x Bv cells (Sec. 3): the bin is the
@@ -64,6 +65,8 @@ __host__ __device__ inline void finish_geometry(Geometry& g, int BU, int BV) {
   g.nvB = g.nv * BV;
   g.mu = (unsigned)((1ull << 31) / (unsigned)g.nu + 1);
   g.mv = (unsigned)((1ull << 31) / (unsigned)g.nv + 1);
+  g.mbu = (unsigned)((1ull << 31) / (unsigned)g.nbu + 1);
+  g.mbv = (unsigned)((1ull << 31) / (unsigned)g.nbv + 1);
 }
 
 // q mod n for 0 <= q < 2^31/n (so for q < 2^15 with any n <= 2^16), with
@@ -725,6 +728,11 @@ struct Contribution {
     float wu[BU], wv[BV];
     load_taps<BU>(tabU + offu, wu);
     load_taps<BV>(tabV + offv, wv);
+    from_taps(wu, wv, vals);
+  }
+
+  // The products of the chosen form from taps and values already loaded.
+  __device__ __forceinline__ void from_taps(const float (&wu)[BU], const float (&wv)[BV], const float2* vals) {
     if constexpr (form == TAP_PRODUCT) {
 #pragma unroll
       for (int j = 0; j < BV; ++j)
