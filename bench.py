@@ -539,9 +539,10 @@ def main():
     # kernel's source file is the one that was captured
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    tkey = ("grid_" + best_grid["schedule"]) if dominant == "grid" else dominant
     if os.path.exists(tpath) and not args.vis:
         try:
-            ent = json.load(open(tpath))["kernels"][dominant]
+            ent = json.load(open(tpath))["kernels"][tkey]
             src = open(os.path.join(ROOT, "paper_1605_07023_gb300", "csrc", ent["source"]), "rb").read()
             if hashlib.sha256(src).hexdigest()[:16] == ent["sha256_16"]:
                 traffic = ent["bytes"]
@@ -626,9 +627,11 @@ def main():
             "grid_fma_frac": fma_fraction(gpa_g, peak), "degrid_fma_frac": fma_fraction(gpa_d, peak),
             "grid_fma_frac_paper_counting": fma_fraction(gpa_g, peak, PAPER_FLOPS_PER_GPA),
             "plain": {"value": p_value, "unit": UNIT, "ms_per_step": p_total / args.steps, "grid_ms": p_g, "degrid_ms": p_d,
-                      "grid_fma_frac": pg_tflops / peak, "kernel": "Romein B=1, 1024 vis per team, global-memory flushes"},
+                      "grid_fma_frac": pg_tflops / peak,
+                      "kernel": "Romein B=1 (chunked schedule, input order), 1024 vis per team, global-memory flushes"},
             "speedup_vs_plain": value / p_value, "grid_speedup_vs_plain": p_g / g_ms,
-            "roofline": {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": "alu", "kernel": gplan.gridder() if dominant == "grid" else dominant,
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_note": "measured in this run: grid_measure_fma_peak (independent FFMA2 chains, 64 warps "
                                       f"per SM); derived {info['sm_count']} SMs x 128 FP32 FMA lanes x 2 flop x "

@@ -68,11 +68,8 @@ enum { GRID_PREC_F32 = 0, GRID_PREC_BF16 = 1, GRID_PREC_F16 = 2 };
 /* Work distribution. */
 enum {
   /* Sec. 4: fixed-size chunks of baseline-ordered visibilities, one team of
-   * threads per chunk. Flushes go straight to the grid in global memory with
-   * atomic adds. Where the team has at most 64 threads, each staged batch of
-   * 32 visibilities is processed in the order of its footprints' first block
-   * (v, then u) rather than the input order, which groups the visibilities
-   * that share a box; the grid is the same up to FP32 summation order. */
+   * threads per chunk, in the input order. Flushes go straight to the grid in
+   * global memory with atomic adds. */
   GRID_SCHED_CHUNKED = 0,
   /* The same chunks, first binned by the grid "patch" (a square region of
    * the grid) their footprints start in. A CTA accumulates one patch plus a
@@ -103,7 +100,17 @@ enum {
    * Degridding with such a plan uses the chunked degridder on the paper's
    * bin for the same (Bu, Bv), or for 2 x 2 blocks where no chunked kernel
    * is built for (Bu, Bv). */
-  GRID_SCHED_LAZY = 3
+  GRID_SCHED_LAZY = 3,
+  /* The chunked schedule with each staged batch of 32 visibilities processed
+   * in the order of its footprints' first block (v, then u) instead of the
+   * input order, so that visibilities sharing a box are neighbours (fewer
+   * flushes where tracks step back and forth across block edges); the grid
+   * is the same up to FP32 summation order. Tap tables are rotated per
+   * (fine row, cell phase), O * bin^2 entries per axis, so that a thread
+   * reads its taps at a fixed offset. Teams of at most 64 threads whose CTA
+   * fits in shared memory (GRID_ERR_UNSUPPORTED otherwise). Degridding with
+   * such a plan uses the chunked degridder. */
+  GRID_SCHED_SORTED = 4
 };
 
 typedef struct {
@@ -226,10 +233,9 @@ int grid_plan_status(grid_plan_t plan, unsigned* flags, int reset);
 
 /*
  * Name of the kernel grid() launches for this plan (host call, no device
- * work): "rotated" (the chunked schedule with phase-rotated tap tables and
- * box-ordered batches, teams of at most 32 threads), "rotated-wide" (the
- * same, 33..64 threads), "chunked" (larger teams), "patch" or "lazy". The
- * string is static; NULL plan gives "".
+ * work): "chunked", "patch", "lazy", "sorted" (GRID_SCHED_SORTED, teams of at
+ * most 32 threads) or "sorted-wide" (33..64 threads). The string is static;
+ * NULL plan gives "".
  */
 const char* grid_plan_gridder(grid_plan_t plan);
 

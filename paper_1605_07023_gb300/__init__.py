@@ -99,7 +99,7 @@ class Plan:
         return out
 
     def gridder(self) -> str:
-        """Name of the kernel grid() launches: rotated, rotated-wide, chunked, patch or lazy."""
+        """Name of the kernel grid() launches: chunked, patch, lazy, sorted or sorted-wide."""
         return _lib.load().grid_plan_gridder(self.handle).decode()
 
     def skipped(self, reset: bool = False) -> int:

@@ -18,7 +18,7 @@ GRID_ERR_NOMEM = -3
 GRID_ERR_CUDA = -4
 
 PREC = {"f32": 0, "bf16": 1, "f16": 2}
-SCHED = {"chunked": 0, "patch": 1, "tile": 2, "lazy": 3}
+SCHED = {"chunked": 0, "patch": 1, "tile": 2, "lazy": 3, "sorted": 4}
 
 EXPORTS = ("grid_plan_desc_init", "grid_plan_create", "grid_plan_create_ex", "grid_plan_destroy", "grid_plan_describe",
            "grid", "degrid", "degrid_weighted", "grid_make_kernel_table", "grid_compute_indices", "grid_plan_skipped", "grid_plan_status", "grid_plan_gridder",

@@ -25,7 +25,9 @@ PATCH_LENGTHS = (32, 64)
 # Gridding schedules tried by default. The patch schedule measured about 5x slower than the chunked
 # one on GB300 (the L2 atomics it saves are not what bounds the chunked kernel), so it is tried only
 # when asked for (tune_grid(..., schedules=GRID_SCHEDULES + ("patch",))).
-GRID_SCHEDULES = ("chunked", "lazy")
+GRID_SCHEDULES = ("chunked", "sorted", "lazy")
+# Sorted-schedule candidates: the shapes whose teams have at most 64 threads at small S are tried with
+# the chunked lengths and CTA sizes; plan creation refuses the others.
 # Lazy-box candidates: block shapes, with the default widened bin, one chunk length and CTA size.
 LAZY_SHAPES = [(4, 2), (2, 4), (4, 4), (8, 4), (4, 8)]
 DEGRID_LENGTHS = (64, 128, 256)
@@ -80,10 +82,11 @@ def plan_kwargs(cfg: dict) -> dict:
 def _candidates(kind: str, schedules=GRID_SCHEDULES):
     for bu, bv in BLOCK_CANDIDATES:
         if kind == "grid":
-            if "chunked" in schedules:
-                for L in CHUNKED_LENGTHS:
-                    for T in CTA_THREADS:
-                        yield dict(schedule="chunked", Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
+            for sched in ("chunked", "sorted"):
+                if sched in schedules:
+                    for L in CHUNKED_LENGTHS:
+                        for T in CTA_THREADS:
+                            yield dict(schedule=sched, Bu=bu, Bv=bv, vis_per_chunk=L, threads=T)
             if "patch" in schedules:
                 for L in PATCH_LENGTHS:
                     yield dict(schedule="patch", Bu=bu, Bv=bv, vis_per_chunk=L)

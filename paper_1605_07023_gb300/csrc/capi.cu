@@ -214,7 +214,7 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   if (d.Bu < 1 || d.Bu > 8 || d.Bv < 1 || d.Bv > 8) return fail(GRID_ERR_INVALID, "B=(%d,%d): must be 1..8", d.Bu, d.Bv);
   if (d.precision < GRID_PREC_F32 || d.precision > GRID_PREC_F16) return fail(GRID_ERR_INVALID, "precision=%d", d.precision);
   if (d.schedule != GRID_SCHED_CHUNKED && d.schedule != GRID_SCHED_PATCH && d.schedule != GRID_SCHED_TILE &&
-      d.schedule != GRID_SCHED_LAZY)
+      d.schedule != GRID_SCHED_LAZY && d.schedule != GRID_SCHED_SORTED)
     return fail(GRID_ERR_INVALID, "schedule=%d", d.schedule);
   if (d.threads % 32 != 0 && (d.schedule == GRID_SCHED_TILE || d.schedule == GRID_SCHED_LAZY))
     return fail(GRID_ERR_INVALID, "threads=%d: the tile and lazy schedules need whole warps", d.threads);
@@ -395,11 +395,16 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     pl->lazy_teams = gl.tpc;
     pl->lazy_smem = sm;
   }
-  if (d.schedule == GRID_SCHED_CHUNKED || d.schedule == GRID_SCHED_TILE) {
-    // the chunked schedule grids with the rotated-table kernel wherever it applies: teams of at
-    // most 64 threads whose CTA fits in shared memory; otherwise with grid_kernel
+  if (d.schedule == GRID_SCHED_SORTED) {
+    // box-ordered batches and rotated tables: teams of at most 64 threads whose CTA fits in
+    // shared memory
     const RotEntry* re = find_rot_kernel(kbu, kbv, d.npol);
-    if (re && g.ts <= 64) {
+    if (!re || g.ts > 64) {
+      const int ts = g.ts;
+      delete pl;
+      return fail(GRID_ERR_UNSUPPORTED, "sorted schedule: %d threads per team (at most 64)", ts);
+    }
+    {
       const void* fn = g.ts <= 32 ? re->fn : re->fn_wide;
       cudaFuncAttributes fa_r;
       e = cudaFuncGetAttributes(&fa_r, fn);
@@ -419,6 +424,10 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
         pl->rot_threads = gr.tpc * g.ts;
         pl->rot_smem = smem_of(gr);
       }
+    }
+    if (!pl->rot_fn) {
+      delete pl;
+      return fail(GRID_ERR_UNSUPPORTED, "sorted schedule: tables and records do not fit in shared memory");
     }
   }
   // word 0: skipped visibilities; word 1: status flags of the lazy gridder
@@ -608,7 +617,7 @@ int grid_plan_skipped(grid_plan_t pl, int64_t* n_skipped, int reset) {
 const char* grid_plan_gridder(grid_plan_t pl) {
   if (!pl) return "";
   if (pl->lazy) return "lazy";
-  if (pl->rot_fn) return pl->g.ts <= 32 ? "rotated" : "rotated-wide";
+  if (pl->rot_fn) return pl->g.ts <= 32 ? "sorted" : "sorted-wide";
   return pl->desc.schedule == GRID_SCHED_PATCH ? "patch" : "chunked";
 }
 

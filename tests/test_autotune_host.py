@@ -11,19 +11,19 @@ from paper_1605_07023_gb300 import autotune
 
 
 def test_grid_candidates_cover_the_gridding_schedules():
-    """By default the chunked and lazy schedules; the patch schedule (about 5x slower on GB300) only
-    when asked for."""
+    """By default the chunked, sorted and lazy schedules; the patch schedule (about 5x slower on GB300)
+    only when asked for."""
     c = list(autotune._candidates("grid"))
-    assert {x["schedule"] for x in c} == {"chunked", "lazy"}
-    c_all = list(autotune._candidates("grid", ("chunked", "patch", "lazy")))
-    assert {x["schedule"] for x in c_all} == {"chunked", "patch", "lazy"}
+    assert {x["schedule"] for x in c} == {"chunked", "sorted", "lazy"}
+    c_all = list(autotune._candidates("grid", ("chunked", "sorted", "patch", "lazy")))
+    assert {x["schedule"] for x in c_all} == {"chunked", "sorted", "patch", "lazy"}
     for x in c_all:
         assert x["vis_per_chunk"] > 0
         if x["schedule"] == "lazy":
             assert (x["Bu"], x["Bv"]) in autotune.LAZY_SHAPES and x["threads"] % 32 == 0
         else:
             assert (x["Bu"], x["Bv"]) in autotune.BLOCK_CANDIDATES
-        if x["schedule"] == "chunked":
+        if x["schedule"] in ("chunked", "sorted"):
             assert x["threads"] in autotune.CTA_THREADS
     # Sec. 6: near-square shapes are the ones worth trying; the list stays within 4:1
     for bu, bv in autotune.BLOCK_CANDIDATES:

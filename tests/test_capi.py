@@ -95,7 +95,7 @@ def test_schedule_and_tile_threads_checked_on_the_host(lib):
     given to a schedule other than the lazy one are rejected before any device call."""
     from paper_1605_07023_gb300 import _lib
     h = ctypes.c_void_p()
-    for sched, threads, bins in [(4, 0, 0), (-1, 0, 0), (_lib.SCHED["tile"], 48, 0), (_lib.SCHED["tile"], 100, 0),
+    for sched, threads, bins in [(5, 0, 0), (-1, 0, 0), (_lib.SCHED["tile"], 48, 0), (_lib.SCHED["tile"], 100, 0),
                                  (_lib.SCHED["lazy"], 48, 0), (_lib.SCHED["chunked"], 0, 10)]:
         d = _lib.GridPlanDesc()
         lib.grid_plan_desc_init(ctypes.byref(d), 256, 7, 8, 4, 2)

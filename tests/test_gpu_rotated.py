@@ -1,5 +1,5 @@
-"""The chunked schedule's rotated-table gridder (box-ordered batches, staged move masks) against the
-FP64 oracle, through the C ABI, on inputs chosen to stress its reordering and its move masks.
+"""The sorted schedule's gridder (box-ordered batches, rotated tap tables, staged move masks) against
+the FP64 oracle, through the C ABI, on inputs chosen to stress its reordering and its move masks.
 
 Bar: relative L2 error <= 1e-5 per polarization plane, and the oracle's count of skipped
 visibilities. Which kernel a plan launches is checked through grid_plan_gridder().
@@ -35,6 +35,7 @@ def kb32(S, O):
 
 def check(gb, w, Bu, Bv, expect=None, **kw):
     table32 = kb32(w.S, w.oversample)
+    kw.setdefault("schedule", "sorted")
     plan = gb.Plan(w.G, w.S, w.oversample, w.npol, Bu=Bu, Bv=Bv, **kw)
     if expect is not None:
         assert plan.gridder() == expect
@@ -74,14 +75,18 @@ def tracks(n, G, S, seed, npol=4, speed=0.7, jitter=1.5):
 
 
 def test_kernel_selection(gb):
-    """The bench shape runs the rotated kernel; 49-thread teams the wide one; larger teams grid_kernel."""
-    assert gb.Plan(2048, 7, 8, 4, B=2, vis_per_chunk=128, threads=128).gridder() == "rotated"
-    assert gb.Plan(2048, 7, 8, 4, B=1).gridder() == "rotated-wide"
-    assert gb.Plan(4096, 15, 16, 1, B=2).gridder() == "rotated-wide"     # 8 x 8 = 64 threads
-    assert gb.Plan(4096, 15, 16, 1, B=1).gridder() == "chunked"          # 225 threads
-    assert gb.Plan(4096, 15, 16, 1, B=4).gridder() == "rotated"          # 5 x 5
+    """Sorted plans run the narrow kernel for teams of up to 32 threads and the wide one up to 64;
+    larger teams are refused. The other schedules keep their own kernels."""
+    assert gb.Plan(2048, 7, 8, 4, B=2, vis_per_chunk=128, threads=128, schedule="sorted").gridder() == "sorted"
+    assert gb.Plan(2048, 7, 8, 4, B=1, schedule="sorted").gridder() == "sorted-wide"          # 7 x 7 = 49
+    assert gb.Plan(4096, 15, 16, 1, B=2, schedule="sorted").gridder() == "sorted-wide"        # 8 x 8 = 64
+    assert gb.Plan(4096, 15, 16, 1, B=4, schedule="sorted").gridder() == "sorted"             # 5 x 5
+    with pytest.raises(gb.GridderError) as e:
+        gb.Plan(4096, 15, 16, 1, B=1, schedule="sorted")                                     # 225 threads
+    assert e.value.code == -2
+    assert gb.Plan(2048, 7, 8, 4, B=2).gridder() == "chunked"
     assert gb.Plan(2048, 7, 8, 4, B=2, schedule="patch").gridder() == "patch"
-    assert gb.Plan(2048, 7, 8, 4, B=2, schedule="tile").gridder() == "rotated"
+    assert gb.Plan(2048, 7, 8, 4, B=2, schedule="tile").gridder() == "chunked"
 
 
 @pytest.mark.parametrize("Bu,Bv", [(2, 2), (1, 1), (2, 1), (4, 2), (3, 3), (4, 4), (8, 2), (1, 8)])
@@ -97,7 +102,7 @@ def test_jittered_tracks(gb, Bu, Bv, npol):
 def test_chunk_lengths_and_ctas(gb, chunk, threads):
     """Chunks that end inside a batch or at its edge, and CTAs of one to sixteen teams."""
     w = tracks(20_011, 256, 7, seed=chunk + threads, npol=4)
-    check(gb, w, 2, 2, "rotated", vis_per_chunk=chunk, threads=threads)
+    check(gb, w, 2, 2, "sorted", vis_per_chunk=chunk, threads=threads)
 
 
 @pytest.mark.parametrize("order", ["reversed", "shuffled", "duplicates", "alternating"])
@@ -158,8 +163,8 @@ def test_sort_key_wraps_on_large_grids(gb):
     uv = np.concatenate([uv, -uv, uv * [1, -1]])
     vis = (rng.standard_normal((len(uv), 1)) + 1j * rng.standard_normal((len(uv), 1))).astype(np.complex64)
     w = synth.Workload("far", G, S, 8, 1, uv, vis, np.ones(len(uv), np.float32))
-    check(gb, w, 1, 1, "rotated-wide")
-    check(gb, w, 2, 2, "rotated")
+    check(gb, w, 1, 1, "sorted-wide")
+    check(gb, w, 2, 2, "sorted")
 
 
 @pytest.mark.parametrize("precision", ["bf16", "f16"])
@@ -171,8 +176,8 @@ def test_16bit_storage(gb, precision):
     vis16 = torch.view_as_real(torch.from_numpy(w.vis)).to(dt)
     tab64 = table.float().double().numpy()
     vis_r = torch.view_as_complex(vis16.float().contiguous()).numpy().astype(np.complex128)
-    plan = gb.Plan(w.G, w.S, w.oversample, 4, B=2, precision=precision)
-    assert plan.gridder() == "rotated"
+    plan = gb.Plan(w.G, w.S, w.oversample, 4, B=2, precision=precision, schedule="sorted")
+    assert plan.gridder() == "sorted"
     g = torch.zeros((4, w.G, w.G), dtype=torch.complex64, device="cuda")
     gb.grid(plan, torch.from_numpy(w.uv).cuda(), vis16.cuda(), torch.from_numpy(w.weights).cuda(), table.cuda(), g)
     torch.cuda.synchronize()
@@ -182,9 +187,7 @@ def test_16bit_storage(gb, precision):
         assert rel_l2(got[p], ref[p]) <= TOL
 
 
-def test_full_size_bench_plan_is_rotated(gb):
-    """The quad-pol workload's bench plan (2x2 blocks, 128 per chunk, 128-thread CTAs) launches the
-    rotated kernel; its full-size parity is checked in test_gpu_parity."""
-    w = synth.quad_pol()
-    plan = gb.Plan(w.G, w.S, w.oversample, 4, B=2, vis_per_chunk=128, threads=128)
-    assert plan.gridder() == "rotated"
+def test_full_quad_pol_sorted(gb):
+    """All 8,257,536 visibilities of the quad-pol workload with the plan the benchmark tunes to (2x2
+    blocks, 128 visibilities per chunk, 128-thread CTAs)."""
+    check(gb, synth.quad_pol(), 2, 2, "sorted", vis_per_chunk=128, threads=128)
