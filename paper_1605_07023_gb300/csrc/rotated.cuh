@@ -53,7 +53,9 @@ struct RotTeamLayout {
   static constexpr unsigned keys = tvals + kRB * P * 8;        // u32 [kRB]
   static constexpr unsigned sortK = keys + kRB * 4;            // u32 [kRB], box order
   static constexpr unsigned mhi = sortK + kRB * 4;             // WIDE: u32 every 16 bytes, box order
-  static constexpr unsigned bytes = mhi + (WIDE ? kRB * 16 : 0);
+  // Team areas are 16 bytes past a multiple of 128, so the broadcast 16-byte loads of the
+  // (up to 8) teams of one warp fall in different shared-memory banks.
+  static constexpr unsigned bytes = (mhi + (WIDE ? kRB * 16 : 0) + 127) / 128 * 128 + 16;
 };
 
 struct RotLayout {
