@@ -543,7 +543,8 @@ def main():
     if os.path.exists(tpath) and not args.vis:
         try:
             ent = json.load(open(tpath))["kernels"][tkey]
-            src = open(os.path.join(ROOT, "paper_1605_07023_gb300", "csrc", ent["source"]), "rb").read()
+            files = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
+            src = b"".join(open(os.path.join(ROOT, "paper_1605_07023_gb300", "csrc", f), "rb").read() for f in files)
             if hashlib.sha256(src).hexdigest()[:16] == ent["sha256_16"]:
                 traffic = ent["bytes"]
         except Exception:
