@@ -560,11 +560,16 @@ int degrid_weighted(grid_plan_t pl, int64_t n_vis, const double* uv, const void*
   void* args[] = {&a};
   cudaError_t e;
   if (pl->tile) {
+    // the tensor maps of this grid (host-side encoding, passed by value)
+    TileMaps maps;
+    if (tile_maps(*pl->tile, grid_in, pl->g.G, pl->g.P, &maps) != 0)
+      return fail(GRID_ERR_CUDA, "degrid (tile): tensor map encoding failed");
+    void* targs[] = {&a, &maps};
     // persistent warps, one group of 32 visibilities at a time: one wave of resident CTAs
     const long long groups = (n_vis + 31) / 32, wpc = pl->tile_threads / 32;
     long long blocks = (groups + wpc - 1) / wpc;
     if (blocks > (long long)pl->sm_count * pl->occ_tile) blocks = (long long)pl->sm_count * pl->occ_tile;
-    e = cudaLaunchKernel(pl->tile->fn, dim3((unsigned)blocks), dim3(pl->tile_threads), args, pl->tile_smem, stream);
+    e = cudaLaunchKernel(pl->tile->fn, dim3((unsigned)blocks), dim3(pl->tile_threads), targs, pl->tile_smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "degrid (tile) kernel launch");
     return GRID_OK;
   }

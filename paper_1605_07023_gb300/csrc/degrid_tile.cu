@@ -16,12 +16,18 @@
 // group into two halves with a smaller tile measured slower.) Warps are
 // persistent and load the next group's positions one group ahead.
 //
-// The box reaches shared memory by bulk asynchronous copies (cp.async.bulk,
-// the TMA unit's untiled form): one copy per box row and polarization plane,
-// issued by the warp's lanes, completing on the warp's mbarrier.
+// The box reaches shared memory by tiled bulk tensor copies (the TMA unit,
+// cp.async.bulk.tensor) through 3-D tensor maps over this GPU's own [P][G][G]
+// grid: one copy per polarization plane of a box RS cells wide and H rows high
+// (the smallest of three heights that holds the group's rows), completing on
+// the warp's mbarrier. Cells of the box outside the grid are filled with zeros
+// and never read.
 //
 // The index rule, validity, skipped count and output layout are those of the
 // sliding-window degridder.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "kernels.cuh"
 #include "internal.h"
 
@@ -46,9 +52,25 @@ struct TileShape {
   // read different banks (a stride of TW + 1 = 1 mod 16 made every pair one
   // cell apart along a diagonal collide).
   static constexpr int RS = spread_stride(TW);
-  static constexpr int PS = TW * RS;    // plane stride in cells
+  // plane stride in cells: a multiple of 16 (128 bytes), the alignment of a
+  // tensor copy's destination
+  static constexpr int PS = (TW * RS + 15) / 16 * 16;
   static constexpr int CELLS = P * PS;  // complex cells per warp
 };
+
+// Box heights of the three tensor maps: the smallest that holds a group's rows
+// is used (a group of 32 baseline-ordered visibilities usually spans a few
+// rows more than S).
+template <int S>
+__host__ __device__ constexpr int tile_height(int i) {
+  return i == 0 ? (S + 3 < S + 13 ? S + 3 : S + 13) : i == 1 ? S + 7 : S + 13;
+}
+
+__device__ __forceinline__ void tensor_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
+}
 
 // s_p for one visibility whose footprint starts at base (cell (x0, y0) of
 // plane 0), with rows RSTRIDE and planes PSTRIDE cells apart.
@@ -77,7 +99,7 @@ __device__ __noinline__ void footprint_dot_global(const float2* base, int G, con
 }
 
 template <int S, int P>
-__global__ void degrid_tile_kernel(Args a) {
+__global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps) {
   using T = TileShape<S, P>;
   extern __shared__ __align__(16) unsigned char smem[];
   const Geometry& g = a.g;
@@ -85,10 +107,12 @@ __global__ void degrid_tile_kernel(Args a) {
   const int ntab = g.O * S;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = load_tap(a.table, a.tab_fmt, i);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* tile = (float2*)(smem + align16((size_t)ntab * 4)) + (size_t)warp * T::CELLS;
+  // the tiles start on a 128-byte boundary (the host adds 128 bytes of slack)
+  const uint32_t tiles0 = (smem_addr(smem) + (uint32_t)align16((size_t)ntab * 4) + 127u) & ~127u;
+  unsigned char* const tiles = smem + (tiles0 - smem_addr(smem));
+  float2* tile = (float2*)tiles + (size_t)warp * T::CELLS;
   // one mbarrier per warp, after all the tiles
-  const uint32_t mbar = smem_addr((float2*)(smem + align16((size_t)ntab * 4)) + (size_t)(blockDim.x >> 5) * T::CELLS) +
-                        8u * warp;
+  const uint32_t mbar = tiles0 + (uint32_t)((blockDim.x >> 5) * T::CELLS * sizeof(float2)) + 8u * warp;
   if (lane == 0) {
     mbar_init(mbar);
     fence_mbar_init();
@@ -98,7 +122,6 @@ __global__ void degrid_tile_kernel(Args a) {
   bool failed = false;  // a copy did not complete in time: later groups read the grid directly
 
   const int G = g.G;
-  const size_t GG = (size_t)G * G;
   const long long n_groups = (a.n_vis + 31) >> 5;
   const long long stride = (long long)gridDim.x * (blockDim.x >> 5);
   // Persistent warps: the position of the next group's visibility is loaded
@@ -142,20 +165,16 @@ __global__ void degrid_tile_kernel(Args a) {
       const int xe = xmin & ~1;                    // first column of the copy
       const int npair = (xmax + S - xe + 1) >> 1;  // cell pairs per row
       const int sy = ymax - ymin + S;
-      if (!failed && 2 * npair <= T::TW && sy <= T::TW && xe + 2 * npair <= G) {
-        // One bulk copy per (plane, row) of the box, 16*npair bytes each, spread over the lanes;
-        // the last group's reads of the tile are ordered before these writes (syncwarp, then a
-        // proxy fence in every issuing lane), and lane 0 announces the byte count first.
-        const uint32_t row_bytes = 16u * (uint32_t)npair;
-        if (lane == 0) mbar_expect(mbar, row_bytes * (uint32_t)(P * sy));
+      if (!failed && 2 * npair <= T::TW && sy <= T::TW) {
+        // One tensor copy per plane of an RS x H box from (xe, ymin); the last group's reads of
+        // the tile are ordered before these writes (syncwarp, then a proxy fence in every
+        // issuing lane), and lane 0 announces the byte count first.
+        const int mi = sy <= maps.h[0] ? 0 : (sy <= maps.h[1] ? 1 : 2);
+        if (lane == 0) mbar_expect(mbar, (uint32_t)(P * maps.h[mi] * T::RS) * 8u);
         __syncwarp();
-        fence_proxy_async();
-        // lane r copies row r of every plane (sy <= TW rows; no division)
-        for (int row = lane; row < sy; row += 32) {
-          const float2* src = a.grid + (size_t)(ymin + row) * G + xe;
-#pragma unroll
-          for (int p = 0; p < P; ++p)
-            bulk_load(smem_addr(tile + p * T::PS + row * T::RS), src + (size_t)p * GG, row_bytes, mbar);
+        if (lane < P) {
+          fence_proxy_async();
+          tensor_load_3d(smem_addr(tile + lane * T::PS), &maps.m[mi], 2 * xe, ymin, lane, mbar);
         }
         if (!mbar_wait(mbar, phase)) {
           failed = true;
@@ -182,7 +201,8 @@ __global__ void degrid_tile_kernel(Args a) {
 
 template <int S, int P>
 TileKernel tile_entry() {
-  return TileKernel{S, P, (const void*)&degrid_tile_kernel<S, P>, TileShape<S, P>::CELLS};
+  return TileKernel{S, P, (const void*)&degrid_tile_kernel<S, P>, TileShape<S, P>::CELLS, TileShape<S, P>::RS,
+                    {tile_height<S>(0), tile_height<S>(1), tile_height<S>(2)}};
 }
 
 #define GB_TILE_ROW(P) \
@@ -200,7 +220,32 @@ const TileKernel* find_tile_kernel(int S, int P) {
 }
 
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps) {
-  return align16((size_t)O * t.S * 4) + (size_t)warps * t.cells * sizeof(float2) + (size_t)warps * 8;
+  return align16((size_t)O * t.S * 4) + 128 + (size_t)warps * t.cells * sizeof(float2) + (size_t)warps * 8;
+}
+
+int tile_maps(const TileKernel& t, const void* grid, int G, int P, TileMaps* out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return -1;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  // [P][G][G] complex64 as FP32 elements: x = 2G floats, y = G rows, z = P planes
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * G, (cuuint64_t)G, (cuuint64_t)P};
+  const cuuint64_t strides[2] = {(cuuint64_t)G * 8, (cuuint64_t)G * G * 8};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int i = 0; i < 3; ++i) {
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * t.rs), (cuuint32_t)t.h[i], 1};
+    out->h[i] = t.h[i];
+    if (encode(&out->m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(grid), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return -2;
+  }
+  return 0;
 }
 
 }  // namespace gbg

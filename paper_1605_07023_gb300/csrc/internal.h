@@ -1,6 +1,7 @@
 // Host-side declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,11 +47,20 @@ const LazyEntry* lazy_kernels_p4(int* n);
 // Tile-gather degridding (degrid_tile.cu), one kernel per (S, P).
 struct TileKernel {
   int S, P;
-  const void* fn;
-  int cells;  // complex cells of one warp's tile
+  const void* fn;   // degrid_tile_kernel(Args, TileMaps)
+  int cells;        // complex cells of one warp's tile
+  int rs;           // tile row stride in cells: the width of a tensor copy's box
+  int h[3];         // box heights of the three tensor maps
+};
+// Tensor maps over one [P][G][G] grid, one per box height (kernel parameter).
+struct TileMaps {
+  CUtensorMap m[3];
+  int h[3];
 };
 const TileKernel* find_tile_kernel(int S, int P);
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps);
+// Encodes the tensor maps of a tile kernel for this grid (host call); 0 on success.
+int tile_maps(const TileKernel& t, const void* grid, int G, int P, TileMaps* out);
 
 cudaError_t launch_fma_peak(int blocks, int threads, int iters, cudaStream_t st);
 double fma_peak_flops_per_launch(int blocks, int threads, int iters);
