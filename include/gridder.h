@@ -80,8 +80,8 @@ enum {
   /* Gridding as GRID_SCHED_CHUNKED. Degridding by tile gather: each warp
    * takes 32 consecutive visibilities, copies the bounding box of their
    * footprints (up to (S+13) x (S+13) cells per polarization) from the grid
-   * into shared memory (bulk asynchronous copies, one per box row and
-   * plane), and each lane sums its own visibility's footprint
+   * into shared memory (tiled tensor copies through tensor maps over the
+   * grid, one per plane), and each lane sums its own visibility's footprint
    * from there, with no reduction between threads (rows first, the separable
    * form of the Sec. 6 remark). A group whose box is larger reads the grid
    * directly. The same results as the chunked degridder up to FP32 rounding.
