@@ -25,6 +25,8 @@
 //
 // The index rule, validity, skipped count and output layout are those of the
 // sliding-window degridder.
+#include <cstring>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -165,7 +167,7 @@ __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps
       const int xe = xmin & ~1;                    // first column of the copy
       const int npair = (xmax + S - xe + 1) >> 1;  // cell pairs per row
       const int sy = ymax - ymin + S;
-      if (!failed && 2 * npair <= T::TW && sy <= T::TW) {
+      if (!failed && maps.ok && 2 * npair <= T::TW && sy <= T::TW) {
         // One tensor copy per plane of an RS x H box from (xe, ymin); the last group's reads of
         // the tile are ordered before these writes (syncwarp, then a proxy fence in every
         // issuing lane), and lane 0 announces the byte count first.
@@ -225,6 +227,7 @@ size_t tile_smem_bytes(const TileKernel& t, int O, int warps) {
 
 int tile_maps(const TileKernel& t, const void* grid, int G, int P, TileMaps* out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  memset(out, 0, sizeof *out);
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -245,6 +248,7 @@ int tile_maps(const TileKernel& t, const void* grid, int G, int P, TileMaps* out
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return -2;
   }
+  out->ok = 1;
   return 0;
 }
 

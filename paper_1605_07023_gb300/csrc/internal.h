@@ -56,10 +56,12 @@ struct TileKernel {
 struct TileMaps {
   CUtensorMap m[3];
   int h[3];
+  int ok;  // 0: no maps (encoding refused, e.g. a grid smaller than a box): every group reads the grid directly
 };
 const TileKernel* find_tile_kernel(int S, int P);
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps);
-// Encodes the tensor maps of a tile kernel for this grid (host call); 0 on success.
+// Encodes the tensor maps of a tile kernel for this grid (host call); 0 on success. On failure
+// out->ok is 0 and the kernel reads every group's footprints from the grid directly.
 int tile_maps(const TileKernel& t, const void* grid, int G, int P, TileMaps* out);
 
 cudaError_t launch_fma_peak(int blocks, int threads, int iters, cudaStream_t st);

@@ -128,6 +128,14 @@ def test_invalid_and_edge_positions(gb):
     assert np.count_nonzero(got[np.all(ref == 0, axis=1)]) == 0
 
 
+@pytest.mark.parametrize("G,S,P", [(16, 7, 1), (24, 7, 4), (32, 15, 2), (40, 9, 4)])
+def test_small_grids(gb, G, S, P):
+    """Grids not much larger than (or smaller than) a tile's box: the tensor copies reach past the
+    right and bottom edges (zero fill), or the maps cannot be encoded and every group reads the grid
+    directly; either way the same sums."""
+    check(gb, synth.random_uniform(G, S, 8, P, 2_000, seed=G + S))
+
+
 @pytest.mark.parametrize("n", [0, 1, 31, 33, 65])
 def test_short_inputs(gb, n):
     base = synth.scaled_down(quad_pol(), 100)
