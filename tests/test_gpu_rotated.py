@@ -191,3 +191,12 @@ def test_full_quad_pol_sorted(gb):
     """All 8,257,536 visibilities of the quad-pol workload with the plan the benchmark tunes to (2x2
     blocks, 128 visibilities per chunk, 128-thread CTAs)."""
     check(gb, synth.quad_pol(), 2, 2, "sorted", vis_per_chunk=128, threads=128)
+
+
+@pytest.mark.parametrize("B", [(2, 2), (4, 4), (8, 2)])
+def test_precision_workload_subset_sorted(gb, B):
+    """S=15, O=16, G=4096 single polarization (the precision workload's first 1,000,000
+    visibilities): teams of 64 (2x2, the wide kernel), 25 (4x4) and 24 (8x2) threads with large
+    rotated tables."""
+    w = synth.scaled_down(synth.precision_single_pol(), 1_000_000)
+    check(gb, w, *B, vis_per_chunk=256)
