@@ -312,9 +312,10 @@ typedef struct {
  * array when unweighted) and vis_out_dev[2], each with room for n
  * visibilities. Uploads go on one copy stream and downloads on another,
  * ordered by events; the grid is shared and rezeroed per step once the
- * previous step's grid went down. Every step has n visibilities. n_steps in
- * 0..64, at most 64 chunks per step. Ordering with `stream` as for
- * grid_degrid_host(). Returns GRID_OK or a negative error code.
+ * previous step's grid went down. Every step has n visibilities. chunk as in
+ * grid_degrid_host(), 0 = 4,194,304 here. n_steps in 0..64, at most 64
+ * chunks per step. Ordering with `stream` as for grid_degrid_host(). Returns
+ * GRID_OK or a negative error code.
  */
 int grid_degrid_host_steps(grid_plan_t gplan, grid_plan_t dplan, int n_steps, const grid_host_step* steps,
                            int64_t n_vis, double* const* uv_dev, void* const* vis_dev, float* const* weights_dev,

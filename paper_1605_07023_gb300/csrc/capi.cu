@@ -797,7 +797,7 @@ int grid_degrid_host_steps(grid_plan_t gp, grid_plan_t dp, int n_steps, const gr
       return fail(GRID_ERR_INVALID, "null device work buffer in set %d", w);
   int rc = check_device(gp);
   if (rc) return rc;
-  if (chunk == 0) chunk = 1 << 20;
+  if (chunk == 0) chunk = 1 << 22;  // across steps the copies overlap anyway: fewer, larger pieces measured faster
   const long long nc = n_vis > 0 ? (n_vis + chunk - 1) / chunk : 0;
   if (nc > 64) return fail(GRID_ERR_INVALID, "%lld chunks: use a larger chunk (at most 64 per step)", nc);
   cudaError_t e = cudaSuccess;

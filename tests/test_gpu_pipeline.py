@@ -80,9 +80,9 @@ def test_pipelined_pass_empty_and_mismatch(gb):
                             torch.empty((100, 1), dtype=torch.complex64).pin_memory())
 
 
-@pytest.mark.parametrize("dsched", ["chunked", "tile"])
+@pytest.mark.parametrize("dsched,chunk", [("chunked", 32_768), ("tile", 32_768), ("tile", 0)])
 @pytest.mark.parametrize("weighted", [True, False])
-def test_pipelined_steps_match_oracle(gb, weighted, dsched):
+def test_pipelined_steps_match_oracle(gb, weighted, dsched, chunk):
     base = synth.scaled_down(synth.quad_pol(), 120_001)
     rng = np.random.default_rng(22)
     t64 = oracle.kb_table(base.S, base.oversample, base.beta).astype(np.float32).astype(np.float64)
@@ -99,7 +99,7 @@ def test_pipelined_steps_match_oracle(gb, weighted, dsched):
                           grid_out=torch.empty((base.npol, base.G, base.G), dtype=torch.complex64).pin_memory()))
         want.append((vis, wt))
     g = torch.zeros((base.npol, base.G, base.G), dtype=torch.complex64, device="cuda")
-    gb.grid_degrid_host_steps(gplan, dplan, steps, table, g, chunk=32_768)
+    gb.grid_degrid_host_steps(gplan, dplan, steps, table, g, chunk=chunk)   # 0: the default chunk
     torch.cuda.synchronize()
     for st, (vis, wt) in zip(steps, want):
         ref_g, _ = oracle.grid(base.G, base.S, base.oversample, base.uv, vis, wt, t64)
