@@ -892,7 +892,9 @@ __global__ void grid_kernel(Args a) {
       float2* const vlb = (b & 1) ? vl1 : vl0;
       stage_batch<BU, BV, P>(a, vbeg, vend, b, l, mtb, vlb);
       group_sync(a, wmask);
-#pragma unroll 1
+      // single polarization: few packed FMAs per record, so the loop is unrolled to
+      // overlap records (measured 3-4% faster on the S=15 workload); otherwise not
+#pragma unroll (P == 1 ? 4 : 1)
       for (int r = 0; r < kRB; ++r) {
         const int4 m = mtb[r];
         if (m.x == (int)kInvalid) continue;
@@ -1312,7 +1314,7 @@ __device__ __forceinline__ void batch_unit(const BatchArgs& b, const int4 u, con
     if (team < g.tpc) stage_batch<BU, BV, P, kRBB>(a, vbeg, vend, bt, l, mtb, vlb);
     __syncthreads();
     if (active) {
-#pragma unroll 1
+#pragma unroll (P == 1 ? 4 : 1)
       for (int r = 0; r < kRBB; ++r) {
         const int4 m = mtb[r];
         if (m.x == (int)kInvalid) continue;
