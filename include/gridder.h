@@ -26,6 +26,10 @@
  *    - vis: [n][npol] complex, interleaved (re, im). Stored as float32
  *      (GRID_PREC_F32), or as bf16 / fp16 pairs.
  *    - weights: [n] float32.
+ *    - Values and weights are expected to be finite. A non-finite one is not
+ *      confined to its footprint: the register blocks that take it also
+ *      cover padding cells, and in the sorted schedule a thread's later
+ *      blocks in the same chunk take it too.
  *    - kernel_table: [O][S] real, float32, or bf16 / fp16 to match the
  *      plan's precision.
  *    - grid: [npol][G][G] complex64, row index v, column index u.

@@ -333,9 +333,21 @@ __global__ void grid_rot_kernel(Args a) {
       const unsigned mw = WIDE ? *sm<unsigned>(smem, mword + (unsigned)r * 16u) : (unsigned)m.w;
       const bool moved = (mw & mybit) != 0u;
       if (moved) {
-        // this thread's block leaves the box: flush it and take the block of
-        // its residue in the new box, which this visibility then starts
-        if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+        // this thread's block leaves the box: flush and clear it, and take the
+        // block of its residue in the new box
+        if (cur != kInvalid) {
+          flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
+          // Cleared by a multiply by zero, so that moved and staying lanes
+          // run the same packed FMAs below. Measured 4% faster than giving
+          // the moved lanes their own assigning multiplies; clearing with
+          // zero constants raised the kernel to 128 registers.
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int j = 0; j < BV; ++j)
+#pragma unroll
+              for (int i = 0; i < BU; ++i) acc[p][j][i] = __fmul2_rn(acc[p][j][i], make_float2(0.f, 0.f));
+        }
         const int qu = m.z & 0xFFFF, qv = (int)((unsigned)m.z >> 16);
         int du = au - mod_small(qu, g.nu, g.mu);
         int dv = av - mod_small(qv, g.nv, g.mv);
@@ -350,8 +362,7 @@ __global__ void grid_rot_kernel(Args a) {
       load_vals<P>(sm<float2>(smem, tb + TL::vals) + r * P, v);
       Contribution<BU, BV, P> c;
       c.from_taps(wu, wv, v);
-      if (moved) c.template apply<false>(acc);
-      else c.template apply<true>(acc);
+      c.template apply<true>(acc);
     }
   }
   if (cur != kInvalid) flush_global<BU, BV, P, false>(acc, cur, a.grid, g.G);
