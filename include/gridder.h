@@ -89,7 +89,11 @@ enum {
    * from there, with no reduction between threads (rows first, the separable
    * form of the Sec. 6 remark). A group whose box is larger reads the grid
    * directly. The same results as the chunked degridder up to FP32 rounding.
-   * Built for odd S <= 15; threads must be a multiple of 32. */
+   * Odd S <= 15 have unrolled kernels; every other S runs a kernel that
+   * reads S at run time (taps from shared memory), while one warp's tile
+   * (at most 8*P*(S+13)*(S+24) bytes) and the [O][S] table fit in shared
+   * memory (GRID_ERR_UNSUPPORTED otherwise). threads must be a multiple of
+   * 32; the CTA is cut to the warps whose tiles fit. */
   GRID_SCHED_TILE = 2,
   /* Gridding with the Sec. 4 chunks and a wider bin than Sec. 3 needs
    * (bin_u x bin_v cells, multiples of Bu and Bv, at most 32 threads per

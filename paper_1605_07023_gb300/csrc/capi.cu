@@ -25,6 +25,7 @@ struct grid_plan_s {
   int occ_grid;         // resident gridding CTAs per SM (patch schedule)
   int warp_sync;        // team size divides 32: teams synchronise per warp
   const TileKernel* tile;  // tile schedule: the degridding kernel, its CTA size and shared memory
+  TileKernel tile_any;     // the run-time-support kernel's entry, when `tile` points here
   int tile_threads;
   size_t tile_smem;
   int occ_tile;            // resident tile-degridding CTAs per SM
@@ -325,7 +326,14 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
   }
   if (d.schedule == GRID_SCHED_TILE) {
     const TileKernel* t = find_tile_kernel(d.S, d.npol);
-    if (!t) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "tile schedule: no kernel for S=%d npol=%d (odd S <= 15)", d.S, d.npol); }
+    if (!t) {
+      // no unrolled kernel for this support: the run-time-support one
+      if (tile_kernel_any(d.S, d.npol, &pl->tile_any)) {
+        delete pl;
+        return fail(GRID_ERR_UNSUPPORTED, "tile schedule: no kernel for S=%d npol=%d", d.S, d.npol);
+      }
+      t = &pl->tile_any;
+    }
     cudaFuncAttributes fa_t;
     e = cudaFuncGetAttributes(&fa_t, t->fn);
     if (e != cudaSuccess) { delete pl; return cuda_fail(e, "cudaFuncGetAttributes (tile)"); }

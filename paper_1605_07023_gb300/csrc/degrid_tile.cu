@@ -23,6 +23,10 @@
 // the warp's mbarrier. Cells of the box outside the grid are filled with zeros
 // and never read.
 //
+// Supports S = 1, 3, ..., 15 have fully unrolled kernels (taps in registers);
+// every other support up to 64 runs one kernel per P that reads S from the
+// plan and its taps from the shared-memory table.
+//
 // The index rule, validity, skipped count and output layout are those of the
 // sliding-window degridder.
 #include <cstring>
@@ -37,16 +41,23 @@ namespace gbg {
 namespace {
 
 // The smallest even row stride >= w cells that is 6 or 10 mod 16.
-constexpr int spread_stride(int w) {
-  return (w % 16 == 6 || w % 16 == 10) ? w : spread_stride(w + 1);
+__host__ __device__ constexpr int spread_stride(int w) {
+  while (w % 16 != 6 && w % 16 != 10) ++w;
+  return w;
 }
+
+// Tile side in cells: the box of 32 consecutive visibilities on a baseline
+// track fits unless the track is fast (a larger tile measured faster than
+// S + 9, whose misses cost more than the lost occupancy).
+__host__ __device__ constexpr int tile_side(int S) { return S + 13; }
+
+// Plane stride in cells for row stride rs: a multiple of 16 (128 bytes), the
+// alignment of a tensor copy's destination.
+__host__ __device__ constexpr int tile_plane(int S, int rs) { return (tile_side(S) * rs + 15) / 16 * 16; }
 
 template <int S, int P>
 struct TileShape {
-  // Tile side in cells: the box of 32 consecutive visibilities on a baseline
-  // track fits unless the track is fast (a larger tile measured faster than
-  // S + 9, whose misses cost more than the lost occupancy).
-  static constexpr int TW = S + 13;
+  static constexpr int TW = tile_side(S);
   // Row stride in cells. It is even, so that rows start on 16-byte boundaries
   // (the box is copied in 16-byte pieces). A cell is two 4-byte banks, so cell
   // (row, col) starts at bank pair (RS*row + col) mod 16; with RS = 6 or 10
@@ -54,18 +65,15 @@ struct TileShape {
   // read different banks (a stride of TW + 1 = 1 mod 16 made every pair one
   // cell apart along a diagonal collide).
   static constexpr int RS = spread_stride(TW);
-  // plane stride in cells: a multiple of 16 (128 bytes), the alignment of a
-  // tensor copy's destination
-  static constexpr int PS = (TW * RS + 15) / 16 * 16;
+  static constexpr int PS = tile_plane(S, RS);
   static constexpr int CELLS = P * PS;  // complex cells per warp
 };
 
 // Box heights of the three tensor maps: the smallest that holds a group's rows
 // is used (a group of 32 baseline-ordered visibilities usually spans a few
 // rows more than S).
-template <int S>
-__host__ __device__ constexpr int tile_height(int i) {
-  return i == 0 ? (S + 3 < S + 13 ? S + 3 : S + 13) : i == 1 ? S + 7 : S + 13;
+__host__ __device__ constexpr int tile_height(int S, int i) {
+  return i == 0 ? S + 3 : i == 1 ? S + 7 : tile_side(S);
 }
 
 __device__ __forceinline__ void tensor_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
@@ -92,19 +100,55 @@ __device__ __forceinline__ void footprint_dot(Ptr base, Stride rstride, Stride p
   }
 }
 
-// The direct path for a group whose box does not fit the tile: kept out
-// of line so that it adds no registers to the tile path.
+// The same sums for a support known only at run time, with the taps read
+// from the shared-memory table (tu, tv: the visibility's two table rows),
+// each u tap once per row for all P planes. s must be zero on entry.
+template <int P, typename Ptr, typename Stride>
+__device__ __forceinline__ void footprint_dot_any(Ptr base, Stride rstride, Stride pstride, const float* tu,
+                                                  const float* tv, int S, float2 (&s)[P]) {
+#pragma unroll 1
+  for (int j = 0; j < S; ++j) {
+    const Ptr row = base + (Stride)j * rstride;
+    float2 r[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) r[p] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int i = 0; i < S; ++i) {
+      const float2 t = splat(tu[i]);
+#pragma unroll
+      for (int p = 0; p < P; ++p) r[p] = __ffma2_rn(t, row[(Stride)p * pstride + i], r[p]);
+    }
+    const float2 t = splat(tv[j]);
+#pragma unroll
+    for (int p = 0; p < P; ++p) s[p] = __ffma2_rn(t, r[p], s[p]);
+  }
+}
+
+// The direct paths for a group whose box does not fit the tile: kept out
+// of line so that they add no registers to the tile path.
 template <int S, int P>
 __device__ __noinline__ void footprint_dot_global(const float2* base, int G, const float (&tu)[S],
                                                   const float (&tv)[S], float2 (&s)[P]) {
   footprint_dot<S, P>(base, (size_t)G, (size_t)G * G, tu, tv, s);
 }
 
-template <int S, int P>
+template <int P>
+__device__ __noinline__ void footprint_dot_global_any(const float2* base, int G, const float* tu, const float* tv,
+                                                      int S, float2 (&s)[P]) {
+  footprint_dot_any<P>(base, (size_t)G, (size_t)G * G, tu, tv, S, s);
+}
+
+// SC > 0: support SC, fully unrolled, taps in registers. SC = 0: the plan's
+// support (any S), taps read from the shared-memory table.
+template <int SC, int P>
 __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps) {
-  using T = TileShape<S, P>;
   extern __shared__ __align__(16) unsigned char smem[];
   const Geometry& g = a.g;
+  const int S = SC > 0 ? SC : g.S;
+  const int TW = SC > 0 ? TileShape<SC, P>::TW : tile_side(S);
+  const int RS = SC > 0 ? TileShape<SC, P>::RS : spread_stride(TW);
+  const int PS = SC > 0 ? TileShape<SC, P>::PS : tile_plane(S, RS);
+  const int CELLS = P * PS;
   float* tab = (float*)smem;
   const int ntab = g.O * S;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = load_tap(a.table, a.tab_fmt, i);
@@ -112,9 +156,9 @@ __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps
   // the tiles start on a 128-byte boundary (the host adds 128 bytes of slack)
   const uint32_t tiles0 = (smem_addr(smem) + (uint32_t)align16((size_t)ntab * 4) + 127u) & ~127u;
   unsigned char* const tiles = smem + (tiles0 - smem_addr(smem));
-  float2* tile = (float2*)tiles + (size_t)warp * T::CELLS;
+  float2* tile = (float2*)tiles + (size_t)warp * CELLS;
   // one mbarrier per warp, after all the tiles
-  const uint32_t mbar = tiles0 + (uint32_t)((blockDim.x >> 5) * T::CELLS * sizeof(float2)) + 8u * warp;
+  const uint32_t mbar = tiles0 + (uint32_t)((blockDim.x >> 5) * CELLS * sizeof(float2)) + 8u * warp;
   if (lane == 0) {
     mbar_init(mbar);
     fence_mbar_init();
@@ -149,11 +193,13 @@ __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps
     float2 s[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) s[p] = make_float2(0.f, 0.f);
-    float tu[S], tv[S];
+    float tu[SC > 0 ? SC : 1], tv[SC > 0 ? SC : 1];
+    if constexpr (SC > 0) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      tu[i] = tab[ru * S + i];
-      tv[i] = tab[rv * S + i];
+      for (int i = 0; i < SC; ++i) {
+        tu[i] = tab[ru * SC + i];
+        tv[i] = tab[rv * SC + i];
+      }
     }
     const int xmin = __reduce_min_sync(0xFFFFFFFFu, ok ? x0 : 0x7FFFFFFF);
     const int ymin = __reduce_min_sync(0xFFFFFFFFu, ok ? y0 : 0x7FFFFFFF);
@@ -167,16 +213,16 @@ __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps
       const int xe = xmin & ~1;                    // first column of the copy
       const int npair = (xmax + S - xe + 1) >> 1;  // cell pairs per row
       const int sy = ymax - ymin + S;
-      if (!failed && maps.ok && 2 * npair <= T::TW && sy <= T::TW) {
+      if (!failed && maps.ok && 2 * npair <= TW && sy <= TW) {
         // One tensor copy per plane of an RS x H box from (xe, ymin); the last group's reads of
         // the tile are ordered before these writes (syncwarp, then a proxy fence in every
         // issuing lane), and lane 0 announces the byte count first.
         const int mi = sy <= maps.h[0] ? 0 : (sy <= maps.h[1] ? 1 : 2);
-        if (lane == 0) mbar_expect(mbar, (uint32_t)(P * maps.h[mi] * T::RS) * 8u);
+        if (lane == 0) mbar_expect(mbar, (uint32_t)(P * maps.h[mi] * RS) * 8u);
         __syncwarp();
         if (lane < P) {
           fence_proxy_async();
-          tensor_load_3d(smem_addr(tile + lane * T::PS), &maps.m[mi], 2 * xe, ymin, lane, mbar);
+          tensor_load_3d(smem_addr(tile + lane * PS), &maps.m[mi], 2 * xe, ymin, lane, mbar);
         }
         if (!mbar_wait(mbar, phase)) {
           failed = true;
@@ -184,10 +230,16 @@ __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps
         }
         phase ^= 1u;
         __syncwarp();
-        if (ok && !failed) footprint_dot<S, P>((const float2*)tile + (y0 - ymin) * T::RS + (x0 - xe), T::RS, T::PS, tu, tv, s);
+        if (ok && !failed) {
+          const float2* base = (const float2*)tile + (y0 - ymin) * RS + (x0 - xe);
+          if constexpr (SC > 0) footprint_dot<SC, P>(base, RS, PS, tu, tv, s);
+          else footprint_dot_any<P>(base, RS, PS, tab + ru * S, tab + rv * S, S, s);
+        }
         __syncwarp();  // the tile is refilled for the next group
       } else if (ok) {
-        footprint_dot_global<S, P>((const float2*)a.grid + (size_t)y0 * G + x0, G, tu, tv, s);
+        const float2* base = (const float2*)a.grid + (size_t)y0 * G + x0;
+        if constexpr (SC > 0) footprint_dot_global<SC, P>(base, G, tu, tv, s);
+        else footprint_dot_global_any<P>(base, G, tab + ru * S, tab + rv * S, S, s);
       }
     }
     if (k < a.n_vis) {
@@ -204,7 +256,7 @@ __global__ void degrid_tile_kernel(Args a, const __grid_constant__ TileMaps maps
 template <int S, int P>
 TileKernel tile_entry() {
   return TileKernel{S, P, (const void*)&degrid_tile_kernel<S, P>, TileShape<S, P>::CELLS, TileShape<S, P>::RS,
-                    {tile_height<S>(0), tile_height<S>(1), tile_height<S>(2)}};
+                    {tile_height(S, 0), tile_height(S, 1), tile_height(S, 2)}};
 }
 
 #define GB_TILE_ROW(P) \
@@ -219,6 +271,16 @@ const TileKernel* find_tile_kernel(int S, int P) {
   for (const TileKernel& t : kTileKernels)
     if (t.S == S && t.P == P) return &t;
   return nullptr;
+}
+
+int tile_kernel_any(int S, int P, TileKernel* out) {
+  const void* fn = P == 1 ? (const void*)&degrid_tile_kernel<0, 1>
+                 : P == 2 ? (const void*)&degrid_tile_kernel<0, 2>
+                 : P == 4 ? (const void*)&degrid_tile_kernel<0, 4> : nullptr;
+  if (!fn || S < 1 || S > 64) return -1;
+  const int rs = spread_stride(tile_side(S));
+  *out = TileKernel{S, P, fn, P * tile_plane(S, rs), rs, {tile_height(S, 0), tile_height(S, 1), tile_height(S, 2)}};
+  return 0;
 }
 
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps) {

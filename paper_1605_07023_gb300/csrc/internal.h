@@ -59,6 +59,8 @@ struct TileMaps {
   int ok;  // 0: no maps (encoding refused, e.g. a grid smaller than a box): every group reads the grid directly
 };
 const TileKernel* find_tile_kernel(int S, int P);
+// The run-time-support tile kernel for (S, P), 1 <= S <= 64: 0, or -1 when P is not 1, 2 or 4.
+int tile_kernel_any(int S, int P, TileKernel* out);
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps);
 // Encodes the tensor maps of a tile kernel for this grid (host call); 0 on success. On failure
 // out->ok is 0 and the kernel reads every group's footprints from the grid directly.

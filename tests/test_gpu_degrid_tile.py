@@ -1,7 +1,8 @@
 """Degridding with the tile schedule (one warp per 32 visibilities, footprints gathered from a
 shared-memory copy of their bounding box) against the FP64 oracle.
 
-Covers: every built support S (odd, 1..15) and P in {1, 2, 4}; baseline-ordered tracks (the tile
+Covers: every unrolled support S (odd, 1..15) and P in {1, 2, 4}; supports without an unrolled
+kernel (even, or up to 64) through the run-time-support kernel; baseline-ordered tracks (the tile
 path) and unordered positions (groups too large for the tile read the grid directly); CTA sizes
 of 1 to 8 warps; weights (degrid_weighted); positions outside the valid region and non-finite
 ones (skipped and zero, counted like the oracle); groups cut short by the end of the input; 16-bit
@@ -49,6 +50,8 @@ def random_grid(P, G, seed):
 
 
 def check(gb, w, threads=0, weights=None, seed=0, precision="f32"):
+    # the plan also sets up gridding: 2x2 blocks make a team of more than 1024 threads above S=61
+    B = 2 if w.S <= 40 else 4
     table = kb32(w.S, w.oversample)
     if precision != "f32":
         tdt = torch.bfloat16 if precision == "bf16" else torch.float16
@@ -57,7 +60,7 @@ def check(gb, w, threads=0, weights=None, seed=0, precision="f32"):
     else:
         tab = torch.from_numpy(table.astype(np.float32)).cuda()
     g = random_grid(w.npol, w.G, seed)
-    plan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=2, schedule="tile", threads=threads, precision=precision)
+    plan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=B, schedule="tile", threads=threads, precision=precision)
     uv = torch.from_numpy(np.ascontiguousarray(w.uv)).cuda()
     gd = torch.from_numpy(g).cuda()
     if weights is None:
@@ -149,10 +152,27 @@ def test_short_inputs(gb, n):
     check(gb, synth.scaled_down(quad_pol(), n))
 
 
+@pytest.mark.parametrize("S,P", [(S, P) for P in (1, 4) for S in (2, 4, 8, 16, 17, 24, 31, 33, 48)] + [(64, 1)])
+def test_run_time_supports(gb, S, P):
+    """Supports without an unrolled kernel run the kernel that reads S from the plan and its taps
+    from the shared-memory table; at S=48 and P=4 one warp's tile (137 KB) leaves room for one warp
+    per CTA. (A plan also sets up gridding, whose teams limit S=64 to single polarization here.)"""
+    check(gb, track(S, 8, P, seed=S))
+    check(gb, synth.random_uniform(256, S, 8, P, 2_003, seed=S + 10 * P), threads=128)
+
+
+@pytest.mark.parametrize("G,S,P", [(20, 8, 4), (70, 64, 1), (96, 33, 2), (80, 48, 4)])
+def test_run_time_supports_small_grids(gb, G, S, P):
+    """The run-time-support kernel on grids close to (or smaller than) its box."""
+    check(gb, synth.random_uniform(G, S, 8, P, 1_500, seed=G + S))
+
+
 def test_unsupported_shapes_are_rejected(gb):
-    for S, P, threads in [(2, 1, 0), (17, 1, 0), (7, 4, 48), (7, 4, 100)]:
-        with pytest.raises(gb.GridderError):
-            gb.Plan(256, S, 8, P, B=2, schedule="tile", threads=threads)
+    for S, O, P, threads in [(7, 8, 4, 48), (7, 8, 4, 100), (60, 256, 4, 0)]:
+        # CTAs of a part of a warp; a tile (173 KB) and table (61 KB) that do not fit together
+        with pytest.raises(gb.GridderError) as e:
+            gb.Plan(256, S, O, P, B=4, schedule="tile", threads=threads)
+        assert e.value.code in (-1, -2)
 
 
 def test_tile_plan_grids_like_chunked(gb):
