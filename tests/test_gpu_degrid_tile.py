@@ -161,6 +161,15 @@ def test_run_time_supports(gb, S, P):
     check(gb, synth.random_uniform(256, S, 8, P, 2_003, seed=S + 10 * P), threads=128)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "f16"])
+def test_run_time_support_16bit_taps_and_weights(gb, precision):
+    """The run-time-support kernel with 16-bit taps, and with weights (degrid_weighted)."""
+    check(gb, track(10, 8, 4, seed=7), precision=precision)
+    w = track(16, 16, 2, seed=8)
+    rng = np.random.default_rng(9)
+    check(gb, w, weights=rng.uniform(0.1, 3.0, w.n_vis).astype(np.float32), threads=64)
+
+
 @pytest.mark.parametrize("G,S,P", [(20, 8, 4), (70, 64, 1), (96, 33, 2), (80, 48, 4)])
 def test_run_time_supports_small_grids(gb, G, S, P):
     """The run-time-support kernel on grids close to (or smaller than) its box."""
