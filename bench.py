@@ -413,8 +413,9 @@ def measure_single_pol(gb, torch, dev, peak):
 
 
 def parse_cfg(s):
-    """'schedule:Bu,Bv[:L[:T[:bin_u,bin_v]]]' (L visibilities per chunk, T threads per CTA, bin sides in
-    cells for the lazy schedule) -> plan config dict."""
+    """'schedule:Bu,Bv[:L[:T[:bin_u,bin_v | :group]]]' (L visibilities per chunk, T threads per CTA, bin
+    sides in cells for the lazy schedule, visibilities per warp group for the tile schedule) -> plan
+    config dict."""
     parts = s.split(":")
     bu, bv = (int(x) for x in parts[1].split(","))
     cfg = dict(schedule=parts[0], Bu=bu, Bv=bv)
@@ -422,7 +423,9 @@ def parse_cfg(s):
         cfg["vis_per_chunk"] = int(parts[2])
     if len(parts) > 3:
         cfg["threads"] = int(parts[3])
-    if len(parts) > 4:
+    if len(parts) > 4 and parts[0] == "tile":
+        cfg["tile_group"] = int(parts[4])
+    elif len(parts) > 4:
         cfg["bin_u"], cfg["bin_v"] = (int(x) for x in parts[4].split(","))
     return cfg
 

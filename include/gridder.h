@@ -93,7 +93,8 @@ enum {
    * reads S at run time (taps from shared memory), while one warp's tile
    * (at most 8*P*(S+13)*(S+24) bytes) and the [O][S] table fit in shared
    * memory (GRID_ERR_UNSUPPORTED otherwise). threads must be a multiple of
-   * 32; the CTA is cut to the warps whose tiles fit. */
+   * 32; the CTA is cut to the warps whose tiles fit. tile_group picks 32 or 8
+   * visibilities per warp group. */
   GRID_SCHED_TILE = 2,
   /* Gridding with the Sec. 4 chunks and a wider bin than Sec. 3 needs
    * (bin_u x bin_v cells, multiples of Bu and Bv, at most 32 threads per
@@ -136,6 +137,11 @@ typedef struct {
                        roundup(S + B - 1, B)); 0 = the paper's bin, one block wider along each
                        axis where it leaves a footprint less than a block of room (u first), as
                        long as the team stays within 32 threads */
+  int tile_group;   /* GRID_SCHED_TILE: visibilities per warp group, 32 or 8; 0 = 32. With 8,
+                       four lanes share a visibility (each sums every fourth footprint row, the
+                       partial sums are added by shuffles) and the tile is 8 cells wider: for
+                       tracks that move several cells per visibility, whose groups of 32 do
+                       not fit a tile */
 } grid_plan_desc;
 
 /* Fill `desc` with the defaults for the given problem and coarsening B (Bu = Bv = B). */

@@ -56,14 +56,14 @@ class Plan:
 
     schedule: "chunked" (fixed visibilities per team, global flushes), "patch" (chunks binned by
     grid patch, flushes into a shared-memory window), "tile" (grids as "chunked"; degrids by
-    tile gather, one warp per 32 visibilities, threads a multiple of 32), or "lazy" (grids with a
+    tile gather, one warp per tile_group = 32 or 8 visibilities, threads a multiple of 32), or "lazy" (grids with a
     bin of bin_u x bin_v cells, wider than the paper's, whose box moves only when the footprint
     leaves it; degrids as "chunked").
     """
 
     def __init__(self, G: int, S: int, oversample: int, npol: int, B: int = 1, Bu: int | None = None,
                  Bv: int | None = None, vis_per_chunk: int = 0, threads: int = 0, precision: str = "f32",
-                 schedule: str = "chunked", patch: int = 0, bin_u: int = 0, bin_v: int = 0):
+                 schedule: str = "chunked", patch: int = 0, bin_u: int = 0, bin_v: int = 0, tile_group: int = 0):
         lib = _lib.load()
         d = _lib.GridPlanDesc()
         lib.grid_plan_desc_init(ctypes.byref(d), G, S, oversample, npol, B)
@@ -76,6 +76,7 @@ class Plan:
         d.patch = patch
         d.bin_u = bin_u
         d.bin_v = bin_v
+        d.tile_group = tile_group
         h = ctypes.c_void_p()
         _lib.check(lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)))
         self._h = h

@@ -41,7 +41,7 @@ class GridBatchItem(ctypes.Structure):
 
 class GridPlanDesc(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("G", "S", "oversample", "npol", "Bu", "Bv", "vis_per_chunk", "threads",
-                                             "precision", "schedule", "patch", "bin_u", "bin_v")]
+                                             "precision", "schedule", "patch", "bin_u", "bin_v", "tile_group")]
 
 
 class GridderError(RuntimeError):

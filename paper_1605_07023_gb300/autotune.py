@@ -35,6 +35,7 @@ DEGRID_LENGTHS = (64, 128, 256)
 # register-limited teams be resident per SM.
 CTA_THREADS = (128, 256)
 TILE_THREADS = (32, 64, 128)   # tile-schedule degridding: warps per CTA x 32
+TILE_GROUPS = (32, 8)          # tile-schedule degridding: visibilities per warp group
 
 
 def _cache_path() -> str:
@@ -76,7 +77,7 @@ def save_cache(c: dict) -> None:
 def plan_kwargs(cfg: dict) -> dict:
     return dict(Bu=cfg["Bu"], Bv=cfg["Bv"], schedule=cfg["schedule"], vis_per_chunk=cfg.get("vis_per_chunk", 0),
                 threads=cfg.get("threads", 0), precision=cfg.get("precision", "f32"), bin_u=cfg.get("bin_u", 0),
-                bin_v=cfg.get("bin_v", 0))
+                bin_v=cfg.get("bin_v", 0), tile_group=cfg.get("tile_group", 0))
 
 
 def _candidates(kind: str, schedules=GRID_SCHEDULES):
@@ -98,9 +99,11 @@ def _candidates(kind: str, schedules=GRID_SCHEDULES):
         for bu, bv in LAZY_SHAPES:
             yield dict(schedule="lazy", Bu=bu, Bv=bv, vis_per_chunk=256, threads=128)
     if kind == "degrid":
-        # the tile schedule does not use Bu, Bv or the chunk length for degridding
-        for T in TILE_THREADS:
-            yield dict(schedule="tile", Bu=2, Bv=2, vis_per_chunk=0, threads=T)
+        # the tile schedule does not use Bu, Bv or the chunk length for degridding; groups of 8
+        # visibilities (four lanes each) are for tracks too fast for groups of 32
+        for group in TILE_GROUPS:
+            for T in TILE_THREADS:
+                yield dict(schedule="tile", Bu=2, Bv=2, vis_per_chunk=0, threads=T, tile_group=group)
 
 
 def _time(fn, reps: int) -> float:

@@ -194,7 +194,7 @@ void grid_plan_desc_init(grid_plan_desc* d, int G, int S, int oversample, int np
   memset(d, 0, sizeof *d);
   d->G = G; d->S = S; d->oversample = oversample; d->npol = npol; d->Bu = B; d->Bv = B;
   d->vis_per_chunk = 0; d->threads = 0; d->precision = GRID_PREC_F32; d->schedule = GRID_SCHED_CHUNKED; d->patch = 0;
-  d->bin_u = 0; d->bin_v = 0;
+  d->bin_u = 0; d->bin_v = 0; d->tile_group = 0;
 }
 
 int grid_plan_create(grid_plan_t* out, int G, int S, int oversample, int npol, int B) {
@@ -221,6 +221,8 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     return fail(GRID_ERR_INVALID, "threads=%d: the tile and lazy schedules need whole warps", d.threads);
   if (d.schedule != GRID_SCHED_LAZY && (d.bin_u != 0 || d.bin_v != 0))
     return fail(GRID_ERR_INVALID, "bin_u/bin_v apply to the lazy schedule only");
+  if (d.tile_group != 0 && (d.schedule != GRID_SCHED_TILE || (d.tile_group != 32 && d.tile_group != 8)))
+    return fail(GRID_ERR_INVALID, "tile_group=%d: 32 or 8 (0 = 32), for the tile schedule only", d.tile_group);
   if (d.vis_per_chunk < 0 || d.vis_per_chunk > (1 << 20)) return fail(GRID_ERR_INVALID, "vis_per_chunk=%d", d.vis_per_chunk);
   if (d.threads < 0 || d.threads > 1024) return fail(GRID_ERR_INVALID, "threads=%d", d.threads);
   // the chunked kernels of the plan's shape; a lazy-schedule shape that has none degrids with 2x2 blocks
@@ -325,10 +327,12 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     if (pl->occ_grid < 1) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "gridding kernel cannot be resident with this shape"); }
   }
   if (d.schedule == GRID_SCHED_TILE) {
-    const TileKernel* t = find_tile_kernel(d.S, d.npol);
+    if (d.tile_group == 0) d.tile_group = 32;
+    const int lpv = 32 / d.tile_group;  // lanes per visibility
+    const TileKernel* t = find_tile_kernel(d.S, d.npol, lpv);
     if (!t) {
       // no unrolled kernel for this support: the run-time-support one
-      if (tile_kernel_any(d.S, d.npol, &pl->tile_any)) {
+      if (tile_kernel_any(d.S, d.npol, lpv, &pl->tile_any)) {
         delete pl;
         return fail(GRID_ERR_UNSUPPORTED, "tile schedule: no kernel for S=%d npol=%d", d.S, d.npol);
       }
@@ -572,8 +576,9 @@ int degrid_weighted(grid_plan_t pl, int64_t n_vis, const double* uv, const void*
     TileMaps maps;
     tile_maps(*pl->tile, grid_in, pl->g.G, pl->g.P, &maps);  // on failure maps.ok = 0: direct reads
     void* targs[] = {&a, &maps};
-    // persistent warps, one group of 32 visibilities at a time: one wave of resident CTAs
-    const long long groups = (n_vis + 31) / 32, wpc = pl->tile_threads / 32;
+    // persistent warps, one group of 32 (or 8) visibilities at a time: one wave of resident CTAs
+    const long long gs = 32 / pl->tile->lpv;
+    const long long groups = (n_vis + gs - 1) / gs, wpc = pl->tile_threads / 32;
     long long blocks = (groups + wpc - 1) / wpc;
     if (blocks > (long long)pl->sm_count * pl->occ_tile) blocks = (long long)pl->sm_count * pl->occ_tile;
     e = cudaLaunchKernel(pl->tile->fn, dim3((unsigned)blocks), dim3(pl->tile_threads), targs, pl->tile_smem, stream);

@@ -47,6 +47,7 @@ const LazyEntry* lazy_kernels_p4(int* n);
 // Tile-gather degridding (degrid_tile.cu), one kernel per (S, P).
 struct TileKernel {
   int S, P;
+  int lpv;          // lanes per visibility: 1 (groups of 32 visibilities per warp) or 4 (groups of 8)
   const void* fn;   // degrid_tile_kernel(Args, TileMaps)
   int cells;        // complex cells of one warp's tile
   int rs;           // tile row stride in cells: the width of a tensor copy's box
@@ -58,9 +59,13 @@ struct TileMaps {
   int h[3];
   int ok;  // 0: no maps (encoding refused, e.g. a grid smaller than a box): every group reads the grid directly
 };
-const TileKernel* find_tile_kernel(int S, int P);
-// The run-time-support tile kernel for (S, P), 1 <= S <= 64: 0, or -1 when P is not 1, 2 or 4.
-int tile_kernel_any(int S, int P, TileKernel* out);
+const TileKernel* find_tile_kernel(int S, int P, int lpv);
+// The run-time-support tile kernel for (S, P, lpv), 1 <= S <= 64: 0, or -1 when P is not 1, 2 or 4
+// or lpv not 1 or 4.
+int tile_kernel_any(int S, int P, int lpv, TileKernel* out);
+// The unrolled tile kernels with four lanes per visibility (groups of 8), from their own translation unit.
+const TileKernel* tile_kernels_q(int* n);
+const void* tile_kernel_any_q(int P);
 size_t tile_smem_bytes(const TileKernel& t, int O, int warps);
 // Encodes the tensor maps of a tile kernel for this grid (host call); 0 on success. On failure
 // out->ok is 0 and the kernel reads every group's footprints from the grid directly.

@@ -35,7 +35,9 @@ def test_degrid_candidates_include_the_tile_schedule_in_whole_warps():
     scheds = {x["schedule"] for x in c}
     assert scheds == {"chunked", "tile"}
     tiles = [x for x in c if x["schedule"] == "tile"]
-    assert sorted(x["threads"] for x in tiles) == sorted(autotune.TILE_THREADS)
+    assert sorted((x["threads"], x["tile_group"]) for x in tiles) == sorted(
+        (t, g) for t in autotune.TILE_THREADS for g in autotune.TILE_GROUPS)
+    assert set(autotune.TILE_GROUPS) == {32, 8}
     assert all(x["threads"] % 32 == 0 and 32 <= x["threads"] <= 1024 for x in tiles)
     # no duplicate candidates
     keys = [tuple(sorted(x.items())) for x in c]
@@ -45,7 +47,9 @@ def test_degrid_candidates_include_the_tile_schedule_in_whole_warps():
 def test_plan_kwargs_pass_every_field():
     cfg = dict(schedule="tile", Bu=2, Bv=2, vis_per_chunk=0, threads=64)
     kw = autotune.plan_kwargs(cfg)
-    assert kw == dict(Bu=2, Bv=2, schedule="tile", vis_per_chunk=0, threads=64, precision="f32", bin_u=0, bin_v=0)
+    assert kw == dict(Bu=2, Bv=2, schedule="tile", vis_per_chunk=0, threads=64, precision="f32", bin_u=0, bin_v=0,
+                      tile_group=0)
+    assert autotune.plan_kwargs(dict(cfg, tile_group=8))["tile_group"] == 8
     kw = autotune.plan_kwargs(dict(schedule="lazy", Bu=4, Bv=2, vis_per_chunk=512, threads=128, bin_u=12, bin_v=10))
     assert (kw["schedule"], kw["bin_u"], kw["bin_v"]) == ("lazy", 12, 10)
 

@@ -71,7 +71,7 @@ def test_desc_init_defaults(lib):
     d = _lib.GridPlanDesc()
     lib.grid_plan_desc_init(ctypes.byref(d), 2048, 7, 8, 4, 2)
     assert (d.G, d.S, d.oversample, d.npol, d.Bu, d.Bv) == (2048, 7, 8, 4, 2, 2)
-    assert d.precision == 0 and d.schedule == 0
+    assert d.precision == 0 and d.schedule == 0 and d.tile_group == 0
 
 
 def test_newer_entry_points_reject_bad_arguments(lib):
@@ -103,4 +103,13 @@ def test_schedule_and_tile_threads_checked_on_the_host(lib):
         d.threads = threads
         d.bin_u = bins
         assert lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == _lib.GRID_ERR_INVALID, (sched, threads, bins)
+        assert not h.value
+    # tile groups other than 32 and 8, or given to another schedule
+    for sched, group in [(_lib.SCHED["tile"], 16), (_lib.SCHED["tile"], -8), (_lib.SCHED["chunked"], 8),
+                         (_lib.SCHED["sorted"], 32)]:
+        d = _lib.GridPlanDesc()
+        lib.grid_plan_desc_init(ctypes.byref(d), 256, 7, 8, 4, 2)
+        d.schedule = sched
+        d.tile_group = group
+        assert lib.grid_plan_create_ex(ctypes.byref(h), ctypes.byref(d)) == _lib.GRID_ERR_INVALID, (sched, group)
         assert not h.value

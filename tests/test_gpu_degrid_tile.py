@@ -6,7 +6,8 @@ kernel (even, or up to 64) through the run-time-support kernel; baseline-ordered
 path) and unordered positions (groups too large for the tile read the grid directly); CTA sizes
 of 1 to 8 warps; weights (degrid_weighted); positions outside the valid region and non-finite
 ones (skipped and zero, counted like the oracle); groups cut short by the end of the input; 16-bit
-taps; unsupported shapes and CTA sizes rejected; the full 8,257,536-visibility quad-pol workload.
+taps; unsupported shapes and CTA sizes rejected; the full 8,257,536-visibility quad-pol workload;
+groups of 8 visibilities with four lanes each.
 Tolerance: rel L2 <= 1e-5 per polarization.
 """
 import functools
@@ -49,7 +50,7 @@ def random_grid(P, G, seed):
     return (rng.standard_normal((P, G, G)) + 1j * rng.standard_normal((P, G, G))).astype(np.complex64)
 
 
-def check(gb, w, threads=0, weights=None, seed=0, precision="f32"):
+def check(gb, w, threads=0, weights=None, seed=0, precision="f32", group=0):
     # the plan also sets up gridding: 2x2 blocks make a team of more than 1024 threads above S=61
     B = 2 if w.S <= 40 else 4
     table = kb32(w.S, w.oversample)
@@ -60,7 +61,8 @@ def check(gb, w, threads=0, weights=None, seed=0, precision="f32"):
     else:
         tab = torch.from_numpy(table.astype(np.float32)).cuda()
     g = random_grid(w.npol, w.G, seed)
-    plan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=B, schedule="tile", threads=threads, precision=precision)
+    plan = gb.Plan(w.G, w.S, w.oversample, w.npol, B=B, schedule="tile", threads=threads, precision=precision,
+                   tile_group=group)
     uv = torch.from_numpy(np.ascontiguousarray(w.uv)).cuda()
     gd = torch.from_numpy(g).cuda()
     if weights is None:
@@ -199,8 +201,33 @@ def test_tile_plan_grids_like_chunked(gb):
 
 
 def test_full_quad_pol(gb):
-    """All 8,257,536 visibilities with the tile schedule at 1, 2 and 4 warps per CTA."""
+    """All 8,257,536 visibilities with the tile schedule at 1, 2 and 4 warps per CTA, and in groups
+    of 8."""
     w = quad_pol()
     check(gb, w, threads=32)
     check(gb, w, threads=64, seed=1)
     check(gb, w, threads=128, seed=2)
+    check(gb, w, threads=128, seed=3, group=8)
+
+
+@pytest.mark.parametrize("S", [1, 3, 7, 15, 2, 8, 16, 33])
+@pytest.mark.parametrize("P", [1, 2, 4])
+def test_groups_of_8(gb, S, P):
+    """Groups of 8 visibilities, four lanes per visibility (each summing every fourth footprint row,
+    the partial sums added by shuffles), with unrolled and run-time supports, on tracks and on
+    unordered positions."""
+    check(gb, track(S, 8, P, seed=S), group=8)
+    check(gb, synth.random_uniform(256, S, 8, P, 2_003, seed=S + 10 * P), threads=64, group=8)
+
+
+def test_groups_of_8_fast_tracks(gb):
+    """The precision workload's first 300,000 visibilities (tracks that move several cells per
+    visibility) in groups of 8, with weights and with 16-bit taps; and inputs that end inside a
+    group."""
+    w = synth.scaled_down(synth.precision_single_pol(), 300_000)
+    check(gb, w, group=8)
+    rng = np.random.default_rng(4)
+    check(gb, w, weights=rng.uniform(0.1, 3.0, w.n_vis).astype(np.float32), threads=32, group=8)
+    check(gb, synth.scaled_down(quad_pol(), 40_000), precision="bf16", group=8)
+    for n in (1, 7, 9, 33):
+        check(gb, synth.scaled_down(quad_pol(), n), group=8)
