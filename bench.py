@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain Romein kernel (profiling runs)")
     ap.add_argument("--no-compression", action="store_true", help="skip the compression measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the coarsening sweep and the single-pol comparison")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batching and differentiation workloads")
     return ap.parse_args()
 
 
@@ -412,6 +413,77 @@ def measure_single_pol(gb, torch, dev, peak):
             "paper_context": "Sec. 5: 3.2x single-pol coarsening gain on a GTX 980"}
 
 
+def _event_ms(torch, fn, warmup=2, reps=5):
+    """Median CUDA-event time of fn() on the current stream, after warm-up calls."""
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return sorted(ts)[len(ts) // 2]
+
+
+def measure_batch(gb, torch, dev, peak):
+    """The batching workload (64 channels x 8 w-planes = 512 single-pol grids of 1024^2, S by plane
+    7, 7, 9, 9, 11, 11, 15, 15, 20,000,000 visibilities with uneven counts) in one persistent launch
+    with 2x2 blocks."""
+    ws = [w for row in synth.batched() for w in row]
+    tables = {S: gb.grid_make_kernel_table(S, 8, 2.34 * S, device=dev) for S in sorted({w.S for w in ws})}
+    items = [dict(uv=torch.from_numpy(w.uv).to(dev), vis=torch.from_numpy(w.vis).to(dev),
+                  weights=torch.from_numpy(w.weights).to(dev), table=tables[w.S],
+                  grid=torch.zeros((1, w.G, w.G), dtype=torch.complex64, device=dev), S=w.S) for w in ws]
+    bp = gb.BatchPlan(1024, 8, 1, Bu=2, Bv=2, max_S=15)
+    bp.set(items)
+    ms = _event_ms(torch, bp.execute)
+    gpa = float(sum(w.n_vis * w.S * w.S for w in ws))
+    n = sum(w.n_vis for w in ws)
+    del items, bp
+    torch.cuda.empty_cache()
+    return {"workload": f"batching: 512 single-pol grids of 1024^2 (64 channels x 8 w-planes, S by plane 7,7,9,9,11,11,15,15), "
+                        f"{n:,} vis with uneven counts", "plan": "one persistent launch, 2x2 blocks",
+            "grid_ms": ms, "vis_taps_per_s": gpa / (ms / 1e3), "fma_frac": fma_fraction(gpa / (ms / 1e3), peak)}
+
+
+def measure_differentiation(gb, torch, dev, peak):
+    """The differentiation workload (G=1024, S=7, O=8, P=1, 1,000,000 visibilities): the forward
+    grid, the backward degrid_weighted (tile schedule), and one autograd step through both with an
+    image-domain loss sum |IFFT(grid) - target|^2 (the FFT is PyTorch's)."""
+    from paper_1605_07023_gb300.autograd import grid_op
+    w = synth.differentiation()
+    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta, device=dev)
+    plan = gb.Plan(w.G, w.S, w.oversample, 1, B=2, schedule="tile")
+    uv = torch.from_numpy(w.uv).to(dev)
+    wt = torch.from_numpy(w.weights).to(dev)
+    vis0 = torch.from_numpy(w.vis).to(dev)
+    target = torch.from_numpy(synth.gaussian_sources_image(w.G, 5, seed=0)).to(dev).to(torch.complex64)
+    g = torch.zeros((1, w.G, w.G), dtype=torch.complex64, device=dev)
+
+    def fwd():
+        g.zero_()
+        gb.grid(plan, uv, vis0, wt, table, g)
+
+    def bwd():
+        gb.degrid_weighted(plan, uv, g, table, wt)
+
+    def step():
+        vis = vis0.clone().requires_grad_(True)
+        img = torch.fft.fftshift(torch.fft.ifft2(torch.fft.ifftshift(grid_op(plan, uv, vis, wt, table)[0]), norm="forward"))
+        torch.sum(torch.abs(img - target) ** 2).backward()
+
+    f_ms, b_ms, s_ms = _event_ms(torch, fwd), _event_ms(torch, bwd), _event_ms(torch, step)
+    gpa = float(w.n_vis * w.S * w.S)
+    plan.close()
+    return {"workload": "differentiation: G=1024 S=7 O=8 P=1, 1,000,000 vis", "plan": "2x2 blocks, tile schedule",
+            "grid_ms": f_ms, "degrid_weighted_ms": b_ms, "autograd_step_ms": s_ms,
+            "grid_vis_taps_per_s": gpa / (f_ms / 1e3), "degrid_vis_taps_per_s": gpa / (b_ms / 1e3)}
+
+
 def parse_cfg(s):
     """'schedule:Bu,Bv[:L[:T[:bin_u,bin_v | :group]]]' (L visibilities per chunk, T threads per CTA, bin
     sides in cells for the lazy schedule, visibilities per warp group for the tile schedule) -> plan
@@ -518,7 +590,7 @@ def main():
         p_total, p_g, p_d = timed(pplan, pplan, args.steps, args.warmup)
     p_value = 2.0 * n_valid * S2 / (p_total / args.steps / 1e3)
 
-    sweep = single = None
+    sweep = single = batch = diff = None
     info = gb.device_info()
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or info["max_clock_khz"] / 1e3
@@ -537,6 +609,9 @@ def main():
     if not args.no_sweep and not args.vis:
         sweep = measure_sweep(gb, w, uv, vis, wt, table, grid_buf, n_valid, peak)
         single = measure_single_pol(gb, torch, dev, peak)
+    if not args.no_extra and not args.vis:
+        batch = measure_batch(gb, torch, dev, peak)
+        diff = measure_differentiation(gb, torch, dev, peak)
 
     # DRAM bytes per launch from one ncu capture (profiles/traffic.json), used only while the
     # kernel's source file is the one that was captured
@@ -655,6 +730,10 @@ def main():
             line["sweep"] = sweep
         if single is not None:
             line["single_pol"] = single
+        if batch is not None:
+            line["batch"] = batch
+        if diff is not None:
+            line["differentiation"] = diff
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
