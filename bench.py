@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain Romein kernel (profiling runs)")
     ap.add_argument("--no-compression", action="store_true", help="skip the compression measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the coarsening sweep and the single-pol comparison")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batching and differentiation workloads")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batching, differentiation and small workloads")
     return ap.parse_args()
 
 
@@ -403,11 +403,20 @@ def measure_single_pol(gb, torch, dev, peak):
         if best is None or ms < best[0]:
             best = (ms, bu, bv, L, T)
     ms, bu, bv, L, T = best
-    del uv, vis, wt, g
+    # degridding of the same workload: the sliding-window degridder and the tile gather in groups of 8
+    out = torch.empty((w.n_vis, 1), dtype=torch.complex64, device=dev)
+    degrid = {}
+    for name, kw in (("chunked 4x4", dict(B=4, vis_per_chunk=64, threads=128)),
+                     ("tile, groups of 8", dict(B=2, schedule="tile", threads=64, tile_group=8))):
+        plan = gb.Plan(w.G, w.S, w.oversample, 1, **kw)
+        degrid[name] = _event_ms(torch, lambda: gb.degrid(plan, uv, g, table, out))
+        plan.close()
+    del uv, vis, wt, g, out
     torch.cuda.empty_cache()
     return {"workload": "precision single-pol: G=4096 S=15 O=16 P=1, 256 antennas, 32,640 bl x 256 t x 2 ch = "
                         "16,711,680 vis, FP32", "plain_grid_ms": p_ms,
             "coarsened": {"Bu": bu, "Bv": bv, "vis_per_chunk": L, "threads": T, "grid_ms": ms},
+            "degrid_ms": degrid,
             "gain": p_ms / ms, "plain_fma_frac": fma_fraction(gpa / (p_ms / 1e3), peak),
             "coarsened_fma_frac": fma_fraction(gpa / (ms / 1e3), peak),
             "paper_context": "Sec. 5: 3.2x single-pol coarsening gain on a GTX 980"}
@@ -427,6 +436,31 @@ def _event_ms(torch, fn, warmup=2, reps=5):
         b.synchronize()
         ts.append(a.elapsed_time(b))
     return sorted(ts)[len(ts) // 2]
+
+
+def measure_small(gb, torch, dev):
+    """The small single-pol case (G=256, S=7, O=8, P=1, 30,720 visibilities; launch latency dominates):
+    the plain Romein gridder (B=1, 1024 visibilities per team), the coarsened one (2x2, 32 per team),
+    and the sliding-window and tile degridders."""
+    w = synth.plain_single_pol()
+    uv = torch.from_numpy(w.uv).to(dev)
+    vis = torch.from_numpy(w.vis).to(dev)
+    wt = torch.from_numpy(w.weights).to(dev)
+    table = gb.grid_make_kernel_table(w.S, w.oversample, w.beta, device=dev)
+    g = torch.zeros((1, w.G, w.G), dtype=torch.complex64, device=dev)
+    out = torch.empty((w.n_vis, 1), dtype=torch.complex64, device=dev)
+    res = {"workload": "plain single-pol: G=256 S=7 O=8 P=1, 16 antennas, 120 bl x 256 t = 30,720 vis"}
+    for name, kw, op in (("plain_grid_ms", dict(B=1, vis_per_chunk=1024), "grid"),
+                         ("coarsened_grid_ms", dict(B=2, vis_per_chunk=32), "grid"),
+                         ("degrid_ms", dict(B=2, vis_per_chunk=32), "degrid"),
+                         ("tile_degrid_ms", dict(B=2, schedule="tile"), "degrid")):
+        plan = gb.Plan(w.G, w.S, w.oversample, 1, **kw)
+        if op == "grid":
+            res[name] = _event_ms(torch, lambda: gb.grid(plan, uv, vis, wt, table, g))
+        else:
+            res[name] = _event_ms(torch, lambda: gb.degrid(plan, uv, g, table, out))
+        plan.close()
+    return res
 
 
 def measure_batch(gb, torch, dev, peak):
@@ -590,7 +624,7 @@ def main():
         p_total, p_g, p_d = timed(pplan, pplan, args.steps, args.warmup)
     p_value = 2.0 * n_valid * S2 / (p_total / args.steps / 1e3)
 
-    sweep = single = batch = diff = None
+    sweep = single = batch = diff = small = None
     info = gb.device_info()
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or info["max_clock_khz"] / 1e3
@@ -612,6 +646,7 @@ def main():
     if not args.no_extra and not args.vis:
         batch = measure_batch(gb, torch, dev, peak)
         diff = measure_differentiation(gb, torch, dev, peak)
+        small = measure_small(gb, torch, dev)
 
     # DRAM bytes per launch from one ncu capture (profiles/traffic.json), used only while the
     # kernel's source file is the one that was captured
@@ -734,6 +769,8 @@ def main():
             line["batch"] = batch
         if diff is not None:
             line["differentiation"] = diff
+        if small is not None:
+            line["small"] = small
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
