@@ -384,7 +384,11 @@ int grid_plan_create_ex(grid_plan_t* out, const grid_plan_desc* din) {
     gl.mv = (unsigned)((1ull << 31) / (unsigned)gl.nv + 1);
     gl.mbu = (unsigned)((1ull << 31) / (unsigned)gl.nbu + 1);
     gl.mbv = (unsigned)((1ull << 31) / (unsigned)gl.nbv + 1);
-    if (gl.ts > 32) { delete pl; return fail(GRID_ERR_UNSUPPORTED, "lazy schedule: %d threads per team (more than a warp)", gl.ts); }
+    if (gl.ts > 32) {
+      const int ts = gl.ts;  // gl belongs to the plan
+      delete pl;
+      return fail(GRID_ERR_UNSUPPORTED, "lazy schedule: %d threads per team (more than a warp)", ts);
+    }
     int seg = 1;
     while (seg < gl.ts) seg <<= 1;
     cudaFuncAttributes fa_l;
